@@ -1,0 +1,176 @@
+/*
+ * chem.h -- C ABI of libchem: batched implicit chemistry step on sm_103a.
+ *
+ * The operation is the chemistry half of the operator-split reacting-flow
+ * step of Le & Cambier, "Development of a Flow Solver with Complex Kinetics
+ * on the Graphic Processing Units" (arXiv 1110.4903): Eq. 4 splits the time
+ * derivative into convection and chemistry; the chemistry half advances,
+ * independently in every finite-volume cell, the species densities rho_s and
+ * the energy e (Eq. 3, formation energy excluded) over one fluid time step
+ * dt at constant volume, with the sources of Sec. 3.2 (Eqs. 23-27) and the
+ * implicit system of Eq. 29 solved by Gaussian elimination.  Here Eq. 29 is
+ * iterated to the full backward-Euler solution by Newton's method with
+ * (N_s+1)x(N_s+1) LU with row partial pivoting, on substeps dt 2^-level.
+ *
+ * Conventions
+ *  - Units SI (kg, m, s, mol, K, J), except the Arrhenius factor A, given in
+ *    CGS mol-cm-s units for the forward order of its reaction (incl. +M).
+ *  - Cell state is structure-of-arrays in device memory: rho_s[s*ld + cell]
+ *    (kg/m^3), e[cell] (J/m^3, sensible energy sum_s rho_s (e_s(T) -
+ *    e_s(298.15 K))).  ld >= n_cells; the caller owns all state buffers.
+ *  - Every function returns CHEM_OK (0) or a negative CHEM_E_* code; no
+ *    function aborts the process.  Per-cell outcomes are CHEM_CELL_* codes.
+ *  - Launching calls are asynchronous and stream-ordered on the cudaStream_t
+ *    passed as `stream` (NULL = legacy default stream); they never
+ *    synchronize, except chem_advance_host, which is synchronous.
+ *  - A cell whose step fails keeps its input values.
+ *  - All pointers are plain addresses; no PyTorch type crosses this ABI.
+ */
+#ifndef CHEM_H
+#define CHEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define CHEM_OK               0
+#define CHEM_E_INVALID_ARG   (-1)   /* NULL pointer, bad size, bad option     */
+#define CHEM_E_BAD_MECHANISM (-2)   /* mechanism fails validation             */
+#define CHEM_E_OOM           (-3)   /* device or host allocation failed       */
+#define CHEM_E_OVER_BUDGET   (-4)   /* request larger than the HBM budget     */
+#define CHEM_E_CUDA          (-5)   /* a CUDA call failed (see chem_last_error_message) */
+#define CHEM_E_TIMEOUT       (-6)   /* a bounded wait ran out                 */
+#define CHEM_E_UNSUPPORTED   (-7)   /* size beyond the kernels' limits        */
+#define CHEM_E_NOT_FOUND     (-8)   /* unknown ticket                         */
+
+/* ---- per-cell status ----------------------------------------------------- */
+#define CHEM_CELL_OK             0
+#define CHEM_CELL_NEWTON_FAILED  1  /* substep halving limit reached          */
+#define CHEM_CELL_T_FAILED       2  /* T of the input state not in [200, 6000] K */
+#define CHEM_CELL_BAD_INPUT      3  /* non-finite value or total density <= 0 */
+#define CHEM_CELL_TOO_MANY_STEPS 4  /* substep attempt budget spent           */
+
+/* ---- limits -------------------------------------------------------------- */
+#define CHEM_MAX_SPECIES    64
+#define CHEM_MAX_REACTIONS  4096
+
+#define CHEM_FP64   0   /* everything in FP64                                  */
+#define CHEM_MIXED  1   /* Jacobian and LU in FP32, residual/rates/T in FP64   */
+
+typedef struct chem_handle_s *chem_handle_t;
+
+/* Reaction mechanism (Sec. 3.2; Appendix A gives one such table).  All
+ * arrays are host memory, read during chem_create and not kept. */
+typedef struct chem_mech_desc {
+    int32_t n_species;            /* N_s, 1..CHEM_MAX_SPECIES                  */
+    int32_t n_reactions;          /* reversible reactions, 0..CHEM_MAX_REACTIONS */
+    int32_t n_elements;           /* 0 disables the element-balance check      */
+    const double  *molar_mass;    /* [N_s] kg/mol, > 0                         */
+    const int32_t *elem_comp;     /* [N_s*n_elements] atoms, may be NULL if n_elements == 0 */
+    const double  *nasa7;         /* [N_s][2][7] NASA-7 a1..a7, low then high range */
+    const double  *t_mid;         /* [N_s] range switch, K (T <= t_mid: low)   */
+    const double  *arr_A;         /* [R] Arrhenius factor, CGS, >= 0 (Eq. 23)  */
+    const double  *arr_beta;      /* [R] temperature exponent                  */
+    const double  *arr_Ea;        /* [R] activation energy, J/mol              */
+    const int32_t *reac_sp;       /* [R*3] reactant species, -1 = unused slot  */
+    const int32_t *reac_nu;       /* [R*3] stoichiometric coefficients 1..3    */
+    const int32_t *prod_sp;       /* [R*3] product species, -1 = unused slot   */
+    const int32_t *prod_nu;       /* [R*3]                                     */
+    const int32_t *third_body;    /* [R] 1 = "+M" reaction (Eq. 25 factor)     */
+    const double  *tb_eff;        /* [R*N_s] efficiencies alpha_rs; NULL = all 1 */
+} chem_mech_desc;
+
+typedef struct chem_options {
+    int32_t precision;        /* CHEM_FP64 or CHEM_MIXED                        */
+    double  rtol;             /* Newton: max_i |dx_i|/(rtol|x_i| + atol_i) <= 1 */
+    double  atol_rel;         /* atol = atol_rel * rho (species), atol_rel * E_scale (energy) */
+    int32_t max_newton;       /* Newton iterations per substep attempt, 1..1000 */
+    int32_t max_halvings;     /* deepest substep level, 0..40                   */
+    int32_t max_attempts;     /* substep attempts per cell, 1..1e6              */
+    int32_t point_implicit;   /* 1: one linearised step per substep (Eq. 29 as printed) */
+    int32_t div_check;        /* 1: abandon a substep whose Newton norm stops falling */
+    int32_t lanes_per_cell;   /* 0 = chosen by the library; else 1,2,4,8,16,32 */
+    int32_t autotune;         /* 1: time the lane choices once and keep the best */
+    int64_t hbm_budget_bytes; /* serving: device bytes requests may hold (0 = 50% of free) */
+} chem_options;
+
+/* Fills *o with the defaults: FP64, rtol 1e-10, atol_rel 1e-12,
+ * max_newton 12, max_halvings 20, max_attempts 1000, point_implicit 0,
+ * div_check 1, lanes_per_cell 0, autotune 0, hbm_budget_bytes 0. */
+int chem_default_options(chem_options *o);
+
+/* Validates the mechanism (index ranges, 1..3 species per side with
+ * coefficients 1..3, element balance when n_elements > 0, cp/R > 1 on
+ * [200, 6000] K so temperature recovery is monotone), builds the derived
+ * device tables and returns a handle.  opts may be NULL (defaults).  Uses the
+ * current CUDA device.  Errors: INVALID_ARG, BAD_MECHANISM, UNSUPPORTED, OOM,
+ * CUDA. */
+int chem_create(const chem_mech_desc *mech, const chem_options *opts, chem_handle_t *out);
+
+/* Waits for the handle's own work, then frees everything the handle owns. */
+int chem_destroy(chem_handle_t h);
+
+/* Advances n_cells cells over dt >= 0 in place (Eq. 4, chemistry half):
+ * rho_s [N_s*n_cells] and e [n_cells], device, ld = n_cells.  n_cells == 0 is
+ * a no-op.  Asynchronous on `stream`. */
+int chem_advance(chem_handle_t h, int64_t n_cells, double *rho_s, double *e, double dt,
+                 void *stream);
+
+typedef struct chem_advance_args {
+    int64_t  n_cells;
+    int64_t  ld;              /* leading dimension of rho_s, >= n_cells (0 = n_cells) */
+    double  *rho_s;           /* device, in/out                                */
+    double  *e;               /* device, in/out                                */
+    double   dt;              /* s, >= 0                                       */
+    const double *T_in;       /* device [n_cells] temperature guesses, or NULL (1500 K) */
+    double  *T_out;           /* device [n_cells] temperature of the result, or NULL */
+    int32_t *status;          /* device [n_cells] CHEM_CELL_* codes, or NULL   */
+    int32_t *newton_iters;    /* device [n_cells] Newton iterations, all attempts, or NULL */
+    int32_t *substeps;        /* device [n_cells] accepted substeps, or NULL   */
+    int32_t *failures;        /* device [n_cells] failed substep attempts, or NULL */
+    void    *stream;          /* cudaStream_t                                  */
+    int32_t  precision;       /* -1 = the handle's; else CHEM_FP64 / CHEM_MIXED */
+    int32_t  lanes_per_cell;  /* 0 = the handle's choice                        */
+} chem_advance_args;
+
+/* chem_advance with strides, temperature guesses and per-cell outputs. */
+int chem_advance_ex(chem_handle_t h, const chem_advance_args *a);
+
+/* Same step on HOST buffers (rho_s [N_s*ld], e, optional T_out/status):
+ * copies to library-owned device buffers, advances, copies back and
+ * synchronizes.  Pinned host memory makes the copies faster. */
+int chem_advance_host(chem_handle_t h, int64_t n_cells, int64_t ld, double *rho_s, double *e,
+                      double dt, double *T_out, int32_t *status);
+
+/* Initial states from temperature T [n], pressure P [n] (Pa) and mass
+ * fractions Y [N_s*ld] (all device): rho = P / (R T sum_s Y_s/M_s) (Dalton's
+ * law, Eq. 5), rho_s = rho Y_s, e from Eq. 3.  Asynchronous on `stream`. */
+int chem_state_from_tpy(chem_handle_t h, int64_t n_cells, int64_t ld, const double *T,
+                        const double *P, const double *Y, double *rho_s, double *e,
+                        void *stream);
+
+/* Temperature of given states (the recovery every step starts with), on
+ * device buffers; T_guess may be NULL.  Asynchronous. */
+int chem_temperature(chem_handle_t h, int64_t n_cells, int64_t ld, const double *rho_s,
+                     const double *e, const double *T_guess, double *T_out, void *stream);
+
+/* Lanes per cell the handle uses for `precision` (after autotuning, if on). */
+int chem_get_lanes_per_cell(chem_handle_t h, int32_t precision, int32_t *lanes);
+
+/* Kernel launches this handle has issued since creation (all entry points). */
+int chem_launch_count(chem_handle_t h, int64_t *count);
+
+/* Human-readable text for a CHEM_E_* code (static storage). */
+const char *chem_strerror(int code);
+
+/* Detail of the last error raised on the calling thread (static per thread). */
+const char *chem_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHEM_H */

@@ -1,0 +1,188 @@
+"""ctypes binding of libchem (include/chem.h): argument marshalling only.
+
+Every step of the chemistry path runs in the library's CUDA kernels; this
+module converts PyTorch device tensors and numpy arrays to plain pointers.
+It raises if the compiled library is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchem.so")
+
+FP64, MIXED = 0, 1
+CELL_OK, CELL_NEWTON_FAILED, CELL_T_FAILED, CELL_BAD_INPUT, CELL_TOO_MANY_STEPS = range(5)
+E_CODES = {0: "ok", -1: "INVALID_ARG", -2: "BAD_MECHANISM", -3: "OOM", -4: "OVER_BUDGET",
+           -5: "CUDA", -6: "TIMEOUT", -7: "UNSUPPORTED", -8: "NOT_FOUND"}
+
+
+class ChemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (E_CODES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class MechDesc(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("n_reactions", C.c_int32), ("n_elements", C.c_int32),
+                ("molar_mass", C.c_void_p), ("elem_comp", C.c_void_p), ("nasa7", C.c_void_p),
+                ("t_mid", C.c_void_p), ("arr_A", C.c_void_p), ("arr_beta", C.c_void_p),
+                ("arr_Ea", C.c_void_p), ("reac_sp", C.c_void_p), ("reac_nu", C.c_void_p),
+                ("prod_sp", C.c_void_p), ("prod_nu", C.c_void_p), ("third_body", C.c_void_p),
+                ("tb_eff", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("rtol", C.c_double), ("atol_rel", C.c_double),
+                ("max_newton", C.c_int32), ("max_halvings", C.c_int32), ("max_attempts", C.c_int32),
+                ("point_implicit", C.c_int32), ("div_check", C.c_int32),
+                ("lanes_per_cell", C.c_int32), ("autotune", C.c_int32),
+                ("hbm_budget_bytes", C.c_int64)]
+
+
+class AdvanceArgs(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("ld", C.c_int64), ("rho_s", C.c_void_p), ("e", C.c_void_p),
+                ("dt", C.c_double), ("T_in", C.c_void_p), ("T_out", C.c_void_p),
+                ("status", C.c_void_p), ("newton_iters", C.c_void_p), ("substeps", C.c_void_p),
+                ("failures", C.c_void_p), ("stream", C.c_void_p), ("precision", C.c_int32),
+                ("lanes_per_cell", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libchem.so is not built (run __graft_entry__.build()); "
+                              "there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        p, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "chem_default_options": [p],
+            "chem_create": [p, p, p],
+            "chem_destroy": [p],
+            "chem_advance": [p, i64, p, p, d, p],
+            "chem_advance_ex": [p, p],
+            "chem_advance_host": [p, i64, i64, p, p, d, p, p],
+            "chem_state_from_tpy": [p, i64, i64, p, p, p, p, p, p],
+            "chem_temperature": [p, i64, i64, p, p, p, p, p],
+            "chem_get_lanes_per_cell": [p, i32, p],
+            "chem_launch_count": [p, p],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.chem_strerror.argtypes = [C.c_int]
+        L.chem_strerror.restype = C.c_char_p
+        L.chem_last_error_message.argtypes = []
+        L.chem_last_error_message.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != 0:
+        raise ChemError(rc, lib().chem_last_error_message().decode())
+    return rc
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    check(lib().chem_default_options(C.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor, or None."""
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Chem:
+    """One mechanism on the current CUDA device (chem_create / chem_destroy)."""
+
+    def __init__(self, mech, **opts):
+        self.mech = mech
+        self._keep = [np.ascontiguousarray(a) for a in (
+            mech.molar_mass.astype(np.float64), mech.elem_comp.astype(np.int32),
+            mech.nasa7.astype(np.float64), mech.t_range[:, 1].astype(np.float64),
+            mech.arr_A.astype(np.float64), mech.arr_beta.astype(np.float64),
+            mech.arr_Ea.astype(np.float64), mech.reac_sp.astype(np.int32),
+            mech.reac_nu.astype(np.int32), mech.prod_sp.astype(np.int32),
+            mech.prod_nu.astype(np.int32), mech.third_body.astype(np.int32),
+            mech.tb_eff.astype(np.float64))]
+        k = self._keep
+        self.desc = MechDesc(mech.ns, mech.nr, mech.ne, *[a.ctypes.data for a in k])
+        self.opts = default_options(**opts)
+        h = C.c_void_p()
+        check(lib().chem_create(C.byref(self.desc), C.byref(self.opts), C.byref(h)))
+        self.h = h
+        self.ns = mech.ns
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(lib().chem_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def advance(self, rho, e, dt, *, n_cells=None, T_in=None, T_out=None, status=None,
+                newton_iters=None, substeps=None, failures=None, precision=-1, lanes=0,
+                stream=None):
+        """In-place step of device tensors rho [ns, ld] and e [>= n] (float64)."""
+        n = int(e.shape[0]) if n_cells is None else int(n_cells)
+        a = AdvanceArgs(n, int(rho.stride(0)), rho.data_ptr(), e.data_ptr(), float(dt),
+                        _ptr(T_in), _ptr(T_out), _ptr(status), _ptr(newton_iters), _ptr(substeps),
+                        _ptr(failures), _stream_ptr(stream), int(precision), int(lanes))
+        check(lib().chem_advance_ex(self.h, C.byref(a)))
+
+    def advance_simple(self, n_cells, rho, e, dt, stream=None):
+        check(lib().chem_advance(self.h, int(n_cells), rho.data_ptr(), e.data_ptr(), float(dt),
+                                 _stream_ptr(stream)))
+
+    def advance_host(self, rho, e, dt, T_out=None, status=None):
+        """Step of HOST numpy arrays rho [ns, ld] and e [n] (synchronous)."""
+        n = e.shape[0]
+        check(lib().chem_advance_host(self.h, n, rho.shape[1], rho.ctypes.data, e.ctypes.data,
+                                      float(dt), None if T_out is None else T_out.ctypes.data,
+                                      None if status is None else status.ctypes.data))
+
+    def state_from_tpy(self, T, P, Y, rho, e, stream=None):
+        n = int(T.shape[0])
+        check(lib().chem_state_from_tpy(self.h, n, int(Y.stride(0)), _ptr(T), _ptr(P), _ptr(Y),
+                                        _ptr(rho), _ptr(e), _stream_ptr(stream)))
+
+    def temperature(self, rho, e, T_out, T_guess=None, stream=None):
+        n = int(e.shape[0])
+        check(lib().chem_temperature(self.h, n, int(rho.stride(0)), _ptr(rho), _ptr(e),
+                                     _ptr(T_guess), _ptr(T_out), _stream_ptr(stream)))
+
+    def lanes(self, precision=FP64):
+        v = C.c_int32()
+        check(lib().chem_get_lanes_per_cell(self.h, precision, C.byref(v)))
+        return v.value
+
+    def launch_count(self):
+        v = C.c_int64()
+        check(lib().chem_launch_count(self.h, C.byref(v)))
+        return v.value

@@ -1,0 +1,733 @@
+// chem_api.cu -- host side of libchem: mechanism validation and derived
+// tables, launch configuration, and the C ABI declared in include/chem.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/chem.h"
+#include "chem_handle.h"
+#include "chem_internal.h"
+
+namespace chem {
+
+const void *be_kernel_fp64(int G);
+const void *be_kernel_mixed(int G);
+long long slot_bytes_host(int ns, int nr, int nD, int jt);
+
+static thread_local char g_errmsg[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_errmsg, sizeof g_errmsg, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(CHEM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// NASA-7 on the host (validation and formation energies)
+static inline void host_nasa(const double *a, double T, double &cpR, double &hRT) {
+    cpR = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+    hRT = a[0] + T * (a[1] / 2 + T * (a[2] / 3 + T * (a[3] / 4 + T * a[4] / 5))) + a[5] / T;
+}
+
+static int validate(const chem_mech_desc *d) {
+    if (!d) return fail(CHEM_E_INVALID_ARG, "mechanism descriptor is NULL");
+    const int ns = d->n_species, nr = d->n_reactions, ne = d->n_elements;
+    if (ns < 1 || nr < 0 || ne < 0) return fail(CHEM_E_INVALID_ARG, "bad sizes ns=%d nr=%d ne=%d", ns, nr, ne);
+    if (ns > CHEM_MAX_SPECIES) return fail(CHEM_E_UNSUPPORTED, "n_species %d > %d", ns, CHEM_MAX_SPECIES);
+    if (nr > CHEM_MAX_REACTIONS) return fail(CHEM_E_UNSUPPORTED, "n_reactions %d > %d", nr, CHEM_MAX_REACTIONS);
+    if (!d->molar_mass || !d->nasa7 || !d->t_mid)
+        return fail(CHEM_E_INVALID_ARG, "species arrays missing");
+    if (nr > 0 && (!d->arr_A || !d->arr_beta || !d->arr_Ea || !d->reac_sp || !d->reac_nu ||
+                   !d->prod_sp || !d->prod_nu || !d->third_body))
+        return fail(CHEM_E_INVALID_ARG, "reaction arrays missing");
+    if (ne > 0 && !d->elem_comp) return fail(CHEM_E_INVALID_ARG, "elem_comp missing");
+    for (int s = 0; s < ns; ++s) {
+        if (!(d->molar_mass[s] > 0) || !std::isfinite(d->molar_mass[s]))
+            return fail(CHEM_E_BAD_MECHANISM, "species %d: molar mass %g", s, d->molar_mass[s]);
+        if (!std::isfinite(d->t_mid[s])) return fail(CHEM_E_BAD_MECHANISM, "species %d: t_mid", s);
+        for (int j = 0; j < 14; ++j)
+            if (!std::isfinite(d->nasa7[s * 14 + j]))
+                return fail(CHEM_E_BAD_MECHANISM, "species %d: NASA-7 coefficient %d not finite", s, j);
+        // cp/R > 1 (cv > 0) on the temperature-recovery bracket keeps e(T)
+        // strictly increasing, so the recovery has one root
+        for (int Ti = (int)kTlo; Ti <= (int)kThi; ++Ti) {
+            const double T = Ti;
+            const double *a = d->nasa7 + s * 14 + (T > d->t_mid[s] ? 7 : 0);
+            double cpR, hRT;
+            host_nasa(a, T, cpR, hRT);
+            if (!(cpR > 1.0))
+                return fail(CHEM_E_BAD_MECHANISM, "species %d: cp/R = %g <= 1 at %g K", s, cpR, T);
+        }
+    }
+    for (int r = 0; r < nr; ++r) {
+        if (!(d->arr_A[r] >= 0) || !std::isfinite(d->arr_A[r]) || !std::isfinite(d->arr_beta[r]) ||
+            !std::isfinite(d->arr_Ea[r]))
+            return fail(CHEM_E_BAD_MECHANISM, "reaction %d: bad Arrhenius data", r);
+        int tot[2] = {0, 0};
+        for (int side = 0; side < 2; ++side) {
+            const int32_t *sp = side ? d->prod_sp : d->reac_sp;
+            const int32_t *nu = side ? d->prod_nu : d->reac_nu;
+            for (int j = 0; j < 3; ++j) {
+                const int s = sp[r * 3 + j];
+                if (s < -1 || s >= ns)
+                    return fail(CHEM_E_BAD_MECHANISM, "reaction %d: species index %d", r, s);
+                if (s < 0) continue;
+                if (nu[r * 3 + j] < 1 || nu[r * 3 + j] > 3)
+                    return fail(CHEM_E_BAD_MECHANISM, "reaction %d: coefficient %d", r, nu[r * 3 + j]);
+                for (int jj = 0; jj < j; ++jj)
+                    if (sp[r * 3 + jj] == s)
+                        return fail(CHEM_E_BAD_MECHANISM, "reaction %d: species %d twice on one side", r, s);
+                tot[side] += nu[r * 3 + j];
+            }
+        }
+        if (tot[0] < 1 || tot[1] < 1 || tot[0] > 3 || tot[1] > 3)
+            return fail(CHEM_E_BAD_MECHANISM, "reaction %d: sides of %d and %d molecules", r, tot[0], tot[1]);
+        if (d->third_body[r] != 0 && d->third_body[r] != 1)
+            return fail(CHEM_E_BAD_MECHANISM, "reaction %d: third_body flag", r);
+        if (d->tb_eff && d->third_body[r])
+            for (int s = 0; s < ns; ++s)
+                if (!std::isfinite(d->tb_eff[(size_t)r * ns + s]))
+                    return fail(CHEM_E_BAD_MECHANISM, "reaction %d: efficiency", r);
+        for (int el = 0; el < ne; ++el) {
+            long bal = 0;
+            for (int j = 0; j < 3; ++j) {
+                if (d->reac_sp[r * 3 + j] >= 0)
+                    bal -= (long)d->reac_nu[r * 3 + j] * d->elem_comp[d->reac_sp[r * 3 + j] * ne + el];
+                if (d->prod_sp[r * 3 + j] >= 0)
+                    bal += (long)d->prod_nu[r * 3 + j] * d->elem_comp[d->prod_sp[r * 3 + j] * ne + el];
+            }
+            if (bal != 0) return fail(CHEM_E_BAD_MECHANISM, "reaction %d: element %d not balanced", r, el);
+        }
+    }
+    return CHEM_OK;
+}
+
+// Derived tables (layouts in chem_internal.h)
+struct HostTables {
+    std::vector<double> thermo, tmid, sp, rxn_d, deff, dEf;
+    std::vector<int> rxn_i, dcol, sp_ptr, sp_ent, jmap, j_ptr, j_ent, col_ptr, col_ent;
+    int nD = 0, nnz = 0;
+};
+
+static void build_tables(const chem_mech_desc *d, HostTables &t) {
+    const int ns = d->n_species, nr = d->n_reactions;
+    t.thermo.assign((size_t)ns * 2 * kThermoStride, 0.0);
+    t.tmid.assign(d->t_mid, d->t_mid + ns);
+    t.sp.assign((size_t)ns * kSpStride, 0.0);
+    std::vector<double> ef(ns);
+    for (int s = 0; s < ns; ++s) {
+        for (int rg = 0; rg < 2; ++rg) {
+            const double *a = d->nasa7 + s * 14 + rg * 7;
+            double *th = &t.thermo[((size_t)s * 2 + rg) * kThermoStride];
+            for (int j = 0; j < 5; ++j) th[j] = a[j];
+            th[5] = a[1] / 2;
+            th[6] = a[2] / 3;
+            th[7] = a[3] / 4;
+            th[8] = a[4] / 5;
+            th[9] = a[5];
+            th[10] = a[2] / 2;
+            th[11] = a[3] / 3;
+            th[12] = a[4] / 4;
+            th[13] = a[6];
+        }
+        const double M = d->molar_mass[s];
+        const double *aref = d->nasa7 + s * 14 + (kTref > d->t_mid[s] ? 7 : 0);
+        double cpR, hRT;
+        host_nasa(aref, kTref, cpR, hRT);
+        ef[s] = kR / M * kTref * (hRT - 1.0);
+        t.sp[s * kSpStride + 0] = M;
+        t.sp[s * kSpStride + 1] = 1.0 / M;
+        t.sp[s * kSpStride + 2] = kR / M;
+        t.sp[s * kSpStride + 3] = ef[s];
+    }
+    // dense net stoichiometry
+    std::vector<int> nuR((size_t)nr * ns, 0), nuP((size_t)nr * ns, 0);
+    for (int r = 0; r < nr; ++r)
+        for (int j = 0; j < 3; ++j) {
+            if (d->reac_sp[r * 3 + j] >= 0) nuR[(size_t)r * ns + d->reac_sp[r * 3 + j]] += d->reac_nu[r * 3 + j];
+            if (d->prod_sp[r * 3 + j] >= 0) nuP[(size_t)r * ns + d->prod_sp[r * 3 + j]] += d->prod_nu[r * 3 + j];
+        }
+    t.rxn_d.assign((size_t)nr * kRxnDStride, 0.0);
+    t.rxn_i.assign((size_t)nr * kRxnIStride, -1);
+    std::vector<int> drxn;   // reaction of each D entry
+    for (int r = 0; r < nr; ++r) {
+        const int tb = d->third_body[r];
+        int order = tb, dnu = 0;
+        double Ef = 0.0;
+        for (int j = 0; j < 3; ++j)
+            if (d->reac_sp[r * 3 + j] >= 0) order += d->reac_nu[r * 3 + j];
+        for (int s = 0; s < ns; ++s) {
+            const int v = nuP[(size_t)r * ns + s] - nuR[(size_t)r * ns + s];
+            dnu += v;
+            Ef += v * d->molar_mass[s] * ef[s];
+        }
+        const double A = d->arr_A[r];
+        double *rd = &t.rxn_d[(size_t)r * kRxnDStride];
+        rd[0] = A > 0 ? std::log(A) + (order - 1) * std::log(1e-6) : -INFINITY;
+        rd[1] = d->arr_beta[r];
+        rd[2] = d->arr_Ea[r] / kR;
+        rd[3] = (double)dnu;
+        rd[4] = Ef;
+        int *ri = &t.rxn_i[(size_t)r * kRxnIStride];
+        int nupack = 0;
+        for (int j = 0; j < 3; ++j) {
+            ri[j] = d->reac_sp[r * 3 + j];
+            ri[3 + j] = d->prod_sp[r * 3 + j];
+            if (ri[j] >= 0) nupack |= d->reac_nu[r * 3 + j] << (2 * j);
+            if (ri[3 + j] >= 0) nupack |= d->prod_nu[r * 3 + j] << (8 + 2 * j);
+        }
+        ri[6] = nupack;
+        // D columns: reactant species, product species, then efficiency species
+        std::vector<int> cols;
+        std::map<int, std::pair<int, int>> slots;   // species -> (rsl, psl)
+        for (int j = 0; j < 3; ++j) {
+            const int s = d->reac_sp[r * 3 + j];
+            if (s < 0) continue;
+            if (!slots.count(s)) { slots[s] = {3, 3}; cols.push_back(s); }
+            slots[s].first = j;
+        }
+        for (int j = 0; j < 3; ++j) {
+            const int s = d->prod_sp[r * 3 + j];
+            if (s < 0) continue;
+            if (!slots.count(s)) { slots[s] = {3, 3}; cols.push_back(s); }
+            slots[s].second = j;
+        }
+        if (tb && d->tb_eff)
+            for (int s = 0; s < ns; ++s)
+                if (d->tb_eff[(size_t)r * ns + s] != 1.0 && !slots.count(s)) {
+                    slots[s] = {3, 3};
+                    cols.push_back(s);
+                }
+        const int doff = t.nD;
+        for (int s : cols) {
+            const auto sl = slots[s];
+            t.dcol.push_back(s | (sl.first << 8) | (sl.second << 10));
+            t.deff.push_back(tb ? (d->tb_eff ? d->tb_eff[(size_t)r * ns + s] : 1.0) - 1.0 : 0.0);
+            t.dEf.push_back(Ef);
+            drxn.push_back(r);
+            ++t.nD;
+        }
+        ri[7] = (tb & 1) | (doff << 1) | ((int)cols.size() << 21);
+    }
+    // species CSR: reactions with nonzero net coefficient
+    t.sp_ptr.assign(ns + 1, 0);
+    for (int s = 0; s < ns; ++s) {
+        for (int r = 0; r < nr; ++r) {
+            const int v = nuP[(size_t)r * ns + s] - nuR[(size_t)r * ns + s];
+            if (v != 0) t.sp_ent.push_back((r << 8) | (v & 0xff));
+        }
+        t.sp_ptr[s + 1] = (int)t.sp_ent.size();
+    }
+    // species-block gather lists: J_sk = M_s sum_r nu_rs D_rk
+    std::vector<std::vector<int>> lists((size_t)ns * ns);
+    for (int j = 0; j < t.nD; ++j) {
+        const int r = drxn[j], k = t.dcol[j] & 0xff;
+        for (int s = 0; s < ns; ++s) {
+            const int v = nuP[(size_t)r * ns + s] - nuR[(size_t)r * ns + s];
+            if (v != 0) lists[(size_t)s * ns + k].push_back((j << 8) | (v & 0xff));
+        }
+    }
+    t.jmap.assign((size_t)ns * ns, -1);
+    t.j_ptr.push_back(0);
+    for (int idx = 0; idx < ns * ns; ++idx) {
+        if (lists[idx].empty()) continue;
+        t.jmap[idx] = t.nnz++;
+        for (int ent : lists[idx]) t.j_ent.push_back(ent);
+        t.j_ptr.push_back((int)t.j_ent.size());
+    }
+    // energy-row column lists
+    t.col_ptr.assign(ns + 1, 0);
+    for (int k = 0; k < ns; ++k) {
+        for (int j = 0; j < t.nD; ++j)
+            if ((t.dcol[j] & 0xff) == k) t.col_ent.push_back(j);
+        t.col_ptr[k + 1] = (int)t.col_ent.size();
+    }
+    // keep every array non-empty so device pointers are valid
+    if (t.nD == 0) { t.dcol.push_back(0); t.deff.push_back(0); t.dEf.push_back(0); }
+    if (t.sp_ent.empty()) t.sp_ent.push_back(0);
+    if (t.j_ent.empty()) t.j_ent.push_back(0);
+    if (t.col_ent.empty()) t.col_ent.push_back(0);
+    if (t.rxn_d.empty()) t.rxn_d.assign(kRxnDStride, 0.0);
+    if (t.rxn_i.empty()) t.rxn_i.assign(kRxnIStride, -1);
+}
+
+// Copies the tables into one device allocation.
+static int upload(const HostTables &t, int ns, int nr, Handle *h) {
+    struct Part { const void *src; size_t bytes; size_t off; };
+    std::vector<Part> parts;
+    size_t total = 0;
+    auto add = [&](const void *src, size_t bytes) {
+        total = (total + 255) / 256 * 256;
+        parts.push_back({src, bytes, total});
+        total += bytes;
+        return parts.size() - 1;
+    };
+    const size_t i_th = add(t.thermo.data(), t.thermo.size() * 8);
+    const size_t i_tm = add(t.tmid.data(), t.tmid.size() * 8);
+    const size_t i_sp = add(t.sp.data(), t.sp.size() * 8);
+    const size_t i_rd = add(t.rxn_d.data(), t.rxn_d.size() * 8);
+    const size_t i_ri = add(t.rxn_i.data(), t.rxn_i.size() * 4);
+    const size_t i_dc = add(t.dcol.data(), t.dcol.size() * 4);
+    const size_t i_de = add(t.deff.data(), t.deff.size() * 8);
+    const size_t i_dE = add(t.dEf.data(), t.dEf.size() * 8);
+    const size_t i_spp = add(t.sp_ptr.data(), t.sp_ptr.size() * 4);
+    const size_t i_spe = add(t.sp_ent.data(), t.sp_ent.size() * 4);
+    const size_t i_jm = add(t.jmap.data(), t.jmap.size() * 4);
+    const size_t i_jp = add(t.j_ptr.data(), t.j_ptr.size() * 4);
+    const size_t i_je = add(t.j_ent.data(), t.j_ent.size() * 4);
+    const size_t i_cp = add(t.col_ptr.data(), t.col_ptr.size() * 4);
+    const size_t i_ce = add(t.col_ent.data(), t.col_ent.size() * 4);
+    cudaError_t e = cudaMalloc(&h->dev_tables, total);
+    if (e != cudaSuccess) return fail(CHEM_E_OOM, "device tables (%zu bytes): %s", total, cudaGetErrorString(e));
+    h->dev_tables_bytes = total;
+    std::vector<char> staging(total, 0);
+    for (const auto &p : parts) memcpy(staging.data() + p.off, p.src, p.bytes);
+    e = cudaMemcpy(h->dev_tables, staging.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "copying mechanism tables");
+    char *b = static_cast<char *>(h->dev_tables);
+    DeviceMech &m = h->mech;
+    m.ns = ns;
+    m.nr = nr;
+    m.nD = t.nD;
+    m.nnz = t.nnz;
+    m.nsp_ent = (int)t.sp_ent.size();
+    m.ncol_ent = (int)t.col_ent.size();
+    m.thermo = (const double *)(b + parts[i_th].off);
+    m.tmid = (const double *)(b + parts[i_tm].off);
+    m.sp = (const double *)(b + parts[i_sp].off);
+    m.rxn_d = (const double *)(b + parts[i_rd].off);
+    m.rxn_i = (const int *)(b + parts[i_ri].off);
+    m.dcol = (const int *)(b + parts[i_dc].off);
+    m.deff = (const double *)(b + parts[i_de].off);
+    m.dEf = (const double *)(b + parts[i_dE].off);
+    m.sp_ptr = (const int *)(b + parts[i_spp].off);
+    m.sp_ent = (const int *)(b + parts[i_spe].off);
+    m.jmap = (const int *)(b + parts[i_jm].off);
+    m.j_ptr = (const int *)(b + parts[i_jp].off);
+    m.j_ent = (const int *)(b + parts[i_je].off);
+    m.col_ptr = (const int *)(b + parts[i_cp].off);
+    m.col_ent = (const int *)(b + parts[i_ce].off);
+    return CHEM_OK;
+}
+
+// Launch shape of the backward-Euler kernel for (precision, G): warps per
+// block and blocks per SM that maximise resident warps within shared memory
+// and registers.
+static int configure(Handle *h, int prec, int G, LaunchCfg &cfg) {
+    const void *fn = prec == CHEM_MIXED ? be_kernel_mixed(G) : be_kernel_fp64(G);
+    if (!fn) return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d not available", G);
+    const int S = 32 / G;
+    const long long sb = slot_bytes_host(h->mech.ns, h->mech.nr, h->mech.nD, prec == CHEM_MIXED ? 4 : 8);
+    int best_warps = 0;
+    LaunchCfg best{};
+    // the attribute is per function and shared by every handle: allow the
+    // device maximum and pass each launch its own size
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)h->max_smem_optin);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    for (int wpb : {8, 4, 2, 1}) {
+        const long long smem = (long long)wpb * S * sb;
+        if (smem > h->max_smem_optin) continue;
+        int blocks = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, wpb * 32, (size_t)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        if (blocks * wpb > best_warps) {
+            best_warps = blocks * wpb;
+            best.fn = fn;
+            best.block = wpb * 32;
+            best.smem = (size_t)smem;
+            best.grid = blocks * h->num_sms;
+            best.G = G;
+        }
+    }
+    if (best_warps == 0)
+        return fail(CHEM_E_UNSUPPORTED, "one cell slot (%lld bytes) exceeds shared memory at %d lanes/cell",
+                    sb, G);
+    cfg = best;
+    return CHEM_OK;
+}
+
+int default_lanes(int ns, int prec) {
+    const int n = ns + 1;
+    (void)prec;
+    if (n <= 12) return 4;
+    if (n <= 24) return 8;
+    return 32;
+}
+
+int get_cfg(Handle *h, int prec, int G, LaunchCfg **out) {
+    const int key = prec * 64 + G;
+    std::lock_guard<std::mutex> lk(h->mu);
+    auto it = h->cfgs.find(key);
+    if (it == h->cfgs.end()) {
+        LaunchCfg c;
+        int rc = configure(h, prec, G, c);
+        if (rc) return rc;
+        it = h->cfgs.emplace(key, c).first;
+    }
+    *out = &it->second;
+    return CHEM_OK;
+}
+
+unsigned long long *next_counter(Handle *h) {
+    const unsigned idx = h->counter_idx.fetch_add(1) % kCounterRing;
+    return h->counters + idx;
+}
+
+}  // namespace chem
+
+using namespace chem;
+
+// ---------------------------------------------------------------------------
+// small kernels: state from (T, P, Y) and temperature of given states
+namespace chem {
+
+__global__ void state_from_tpy_kernel(DeviceMech m, long long n, long long ld, const double *T,
+                                      const double *P, const double *Y, double *rho, double *e) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double Ti = T[i], invT = 1.0 / Ti;
+    double invW = 0.0;
+    for (int s = 0; s < m.ns; ++s) invW += Y[(size_t)s * ld + i] * m.sp[s * kSpStride + 1];
+    const double rt = P[i] / (kR * Ti * invW);
+    double ei = 0.0;
+    for (int s = 0; s < m.ns; ++s) {
+        const double rs = rt * Y[(size_t)s * ld + i];
+        rho[(size_t)s * ld + i] = rs;
+        const double *th = m.thermo + (size_t)(s * 2 + (Ti > m.tmid[s] ? 1 : 0)) * kThermoStride;
+        const double hRT = th[0] + Ti * (th[5] + Ti * (th[6] + Ti * (th[7] + Ti * th[8]))) + th[9] * invT;
+        ei += rs * (m.sp[s * kSpStride + 2] * Ti * (hRT - 1.0) - m.sp[s * kSpStride + 3]);
+    }
+    e[i] = ei;
+}
+
+__global__ void temperature_kernel(DeviceMech m, long long n, long long ld, const double *rho,
+                                   const double *e, const double *Tg, double *Tout) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double lo = kTlo, hi = kThi, T = Tg ? Tg[i] : 1500.0;
+    if (!(T > lo && T < hi)) T = 1500.0;
+    const double ei = e[i];
+    bool ok = false;
+    for (int it = 1; it <= kTmaxIter; ++it) {
+        const double invT = 1.0 / T;
+        double f = 0.0, fp = 0.0;
+        for (int s = 0; s < m.ns; ++s) {
+            const double *th = m.thermo + (size_t)(s * 2 + (T > m.tmid[s] ? 1 : 0)) * kThermoStride;
+            const double cpR = th[0] + T * (th[1] + T * (th[2] + T * (th[3] + T * th[4])));
+            const double hRT = th[0] + T * (th[5] + T * (th[6] + T * (th[7] + T * th[8]))) + th[9] * invT;
+            const double RM = m.sp[s * kSpStride + 2];
+            const double r = rho[(size_t)s * ld + i];
+            f += r * (RM * T * (hRT - 1.0) - m.sp[s * kSpStride + 3]);
+            fp += r * RM * (cpR - 1.0);
+        }
+        f -= ei;
+        if (f == 0.0) { ok = true; break; }
+        if (f > 0.0) hi = T; else lo = T;
+        double Tn = T - f / fp;
+        if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+        const double dT = Tn - T;
+        T = Tn;
+        if (fabs(dT) <= kTtol * T) {
+            ok = !(T <= kTlo * (1.0 + 1e-9) || T >= kThi * (1.0 - 1e-9));
+            break;
+        }
+    }
+    Tout[i] = ok ? T : NAN;
+}
+
+long long slot_bytes_host(int ns, int nr, int nD, int jt) {
+    const int n = ns + 1;
+    long long dbl = 2LL * n + 5LL * ns + 3LL * nr;
+    long long jtn = 3LL * ns + nD + (long long)n * (n + 1);
+    return ((dbl * 8 + jtn * jt) + 15) / 16 * 16;
+}
+
+int launch_step(Handle *h, const chem_advance_args *a, int prec, int G, unsigned long long *counter) {
+    LaunchCfg *cfg = nullptr;
+    int rc = get_cfg(h, prec, G, &cfg);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)a->stream;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing the work counter");
+    StepOptions o{h->opts.rtol, h->opts.atol_rel, h->opts.max_newton, h->opts.max_halvings,
+                  h->opts.max_attempts, h->opts.point_implicit, h->opts.div_check};
+    StepBatch b;
+    b.n_cells = a->n_cells;
+    b.ld = a->ld > 0 ? a->ld : a->n_cells;
+    b.rho = a->rho_s;
+    b.e = a->e;
+    b.dt = a->dt;
+    b.T_in = a->T_in;
+    b.T_out = a->T_out;
+    b.status = a->status;
+    b.newton_iters = a->newton_iters;
+    b.substeps = a->substeps;
+    b.failures = a->failures;
+    b.work_counter = counter;
+    // no more blocks than it takes to give every cell a slot
+    const long long slots_per_block = (long long)(cfg->block / 32) * (32 / cfg->G);
+    long long grid = std::min<long long>(cfg->grid, (b.n_cells + slots_per_block - 1) / slots_per_block);
+    if (grid < 1) grid = 1;
+    void *args[] = {&h->mech, &o, &b};
+    e = cudaLaunchKernel(cfg->fn, dim3((unsigned)grid), dim3(cfg->block), args, cfg->smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
+    h->launches.fetch_add(1);
+    return CHEM_OK;
+}
+
+}  // namespace chem
+
+// ---------------------------------------------------------------------------
+// C ABI
+extern "C" {
+
+int chem_default_options(chem_options *o) {
+    if (!o) return fail(CHEM_E_INVALID_ARG, "options pointer is NULL");
+    o->precision = CHEM_FP64;
+    o->rtol = 1e-10;
+    o->atol_rel = 1e-12;
+    o->max_newton = 12;
+    o->max_halvings = 20;
+    o->max_attempts = 1000;
+    o->point_implicit = 0;
+    o->div_check = 1;
+    o->lanes_per_cell = 0;
+    o->autotune = 0;
+    o->hbm_budget_bytes = 0;
+    return CHEM_OK;
+}
+
+static int check_options(const chem_options *o) {
+    if (o->precision != CHEM_FP64 && o->precision != CHEM_MIXED)
+        return fail(CHEM_E_INVALID_ARG, "precision %d", o->precision);
+    if (!(o->rtol > 0) || !(o->atol_rel >= 0) || !std::isfinite(o->rtol) || !std::isfinite(o->atol_rel))
+        return fail(CHEM_E_INVALID_ARG, "tolerances");
+    if (o->max_newton < 1 || o->max_newton > 1000) return fail(CHEM_E_INVALID_ARG, "max_newton %d", o->max_newton);
+    if (o->max_halvings < 0 || o->max_halvings > 40) return fail(CHEM_E_INVALID_ARG, "max_halvings %d", o->max_halvings);
+    if (o->max_attempts < 1 || o->max_attempts > 1000000) return fail(CHEM_E_INVALID_ARG, "max_attempts %d", o->max_attempts);
+    const int l = o->lanes_per_cell;
+    if (l != 0 && l != 2 && l != 4 && l != 8 && l != 16 && l != 32)
+        return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d (0, 2, 4, 8, 16 or 32)", l);
+    if (o->hbm_budget_bytes < 0) return fail(CHEM_E_INVALID_ARG, "hbm_budget_bytes");
+    return CHEM_OK;
+}
+
+int chem_create(const chem_mech_desc *mech, const chem_options *opts, chem_handle_t *out) {
+    if (!out) return fail(CHEM_E_INVALID_ARG, "output handle pointer is NULL");
+    *out = nullptr;
+    chem_options o;
+    chem_default_options(&o);
+    if (opts) o = *opts;
+    int rc = check_options(&o);
+    if (rc) return rc;
+    rc = validate(mech);
+    if (rc) return rc;
+    Handle *h = new (std::nothrow) Handle();
+    if (!h) return fail(CHEM_E_OOM, "host allocation");
+    h->opts = o;
+    h->ns = mech->n_species;
+    h->nr = mech->n_reactions;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, h->device);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDeviceProperties"); }
+    h->num_sms = prop.multiProcessorCount;
+    h->max_smem_optin = (long long)prop.sharedMemPerBlockOptin;
+    HostTables t;
+    build_tables(mech, t);
+    rc = upload(t, h->ns, h->nr, h);
+    if (rc) { chem_destroy(h); return rc; }
+    e = cudaMalloc(&h->counters, sizeof(unsigned long long) * kCounterRing);
+    if (e != cudaSuccess) { chem_destroy(h); return fail(CHEM_E_OOM, "work counters"); }
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { chem_destroy(h); return cuda_fail(e, "stream"); }
+    for (int prec : {CHEM_FP64, CHEM_MIXED}) {
+        const int G = o.lanes_per_cell ? o.lanes_per_cell : default_lanes(h->ns, prec);
+        h->lanes[prec] = G;
+        LaunchCfg *cfg;
+        rc = get_cfg(h, prec, G, &cfg);
+        if (rc) { chem_destroy(h); return rc; }
+    }
+    *out = h;
+    return CHEM_OK;
+}
+
+int chem_destroy(chem_handle_t hh) {
+    Handle *h = hh;
+    if (!h) return fail(CHEM_E_INVALID_ARG, "handle is NULL");
+    destroy_serving(h);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaDeviceSynchronize();
+    if (h->dev_tables) cudaFree(h->dev_tables);
+    if (h->counters) cudaFree(h->counters);
+    if (h->host_rho) cudaFree(h->host_rho);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return CHEM_OK;
+}
+
+int chem_advance_ex(chem_handle_t hh, const chem_advance_args *a) {
+    Handle *h = hh;
+    if (!h || !a) return fail(CHEM_E_INVALID_ARG, "NULL handle or arguments");
+    if (a->n_cells < 0) return fail(CHEM_E_INVALID_ARG, "n_cells %lld", (long long)a->n_cells);
+    if (a->n_cells == 0) return CHEM_OK;
+    if (!a->rho_s || !a->e) return fail(CHEM_E_INVALID_ARG, "state pointers are NULL");
+    if (a->ld != 0 && a->ld < a->n_cells) return fail(CHEM_E_INVALID_ARG, "ld %lld < n_cells", (long long)a->ld);
+    if (!(a->dt >= 0) || !std::isfinite(a->dt)) return fail(CHEM_E_INVALID_ARG, "dt %g", a->dt);
+    const int prec = a->precision < 0 ? h->opts.precision : a->precision;
+    if (prec != CHEM_FP64 && prec != CHEM_MIXED) return fail(CHEM_E_INVALID_ARG, "precision %d", prec);
+    int G = a->lanes_per_cell ? a->lanes_per_cell : h->lanes[prec];
+    if (G != 2 && G != 4 && G != 8 && G != 16 && G != 32)
+        return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d", G);
+    return launch_step(h, a, prec, G, next_counter(h));
+}
+
+int chem_advance(chem_handle_t h, int64_t n_cells, double *rho_s, double *e, double dt, void *stream) {
+    chem_advance_args a;
+    memset(&a, 0, sizeof a);
+    a.n_cells = n_cells;
+    a.ld = n_cells;
+    a.rho_s = rho_s;
+    a.e = e;
+    a.dt = dt;
+    a.stream = stream;
+    a.precision = -1;
+    return chem_advance_ex(h, &a);
+}
+
+int chem_advance_host(chem_handle_t hh, int64_t n_cells, int64_t ld, double *rho_s, double *e, double dt,
+                      double *T_out, int32_t *status) {
+    Handle *h = hh;
+    if (!h || !rho_s || !e) return fail(CHEM_E_INVALID_ARG, "NULL argument");
+    if (n_cells < 0 || (ld != 0 && ld < n_cells)) return fail(CHEM_E_INVALID_ARG, "sizes");
+    if (n_cells == 0) return CHEM_OK;
+    if (ld == 0) ld = n_cells;
+    std::lock_guard<std::mutex> lk(h->host_mu);
+    const int ns = h->ns;
+    const size_t need = (size_t)n_cells * (ns + 1) * 8 + (size_t)n_cells * (8 + 4);
+    if (need > h->host_bytes) {
+        if (h->host_rho) cudaFree(h->host_rho);
+        h->host_rho = nullptr;
+        h->host_bytes = 0;
+        cudaError_t e2 = cudaMalloc(&h->host_rho, need);
+        if (e2 != cudaSuccess) return fail(CHEM_E_OOM, "staging buffers (%zu bytes)", need);
+        h->host_bytes = need;
+    }
+    double *d_rho = (double *)h->host_rho;
+    double *d_e = d_rho + (size_t)n_cells * ns;
+    double *d_T = d_e + n_cells;
+    int32_t *d_st = (int32_t *)(d_T + n_cells);
+    cudaStream_t st = h->stream;
+    cudaError_t ce = cudaMemcpy2DAsync(d_rho, (size_t)n_cells * 8, rho_s, (size_t)ld * 8, (size_t)n_cells * 8, ns,
+                                       cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "host-to-device copy");
+    ce = cudaMemcpyAsync(d_e, e, (size_t)n_cells * 8, cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "host-to-device copy");
+    chem_advance_args a;
+    memset(&a, 0, sizeof a);
+    a.n_cells = n_cells;
+    a.ld = n_cells;
+    a.rho_s = d_rho;
+    a.e = d_e;
+    a.dt = dt;
+    a.T_out = T_out ? d_T : nullptr;
+    a.status = status ? d_st : nullptr;
+    a.stream = st;
+    a.precision = -1;
+    int rc = chem_advance_ex(h, &a);
+    if (rc) return rc;
+    ce = cudaMemcpy2DAsync(rho_s, (size_t)ld * 8, d_rho, (size_t)n_cells * 8, (size_t)n_cells * 8, ns,
+                           cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(e, d_e, (size_t)n_cells * 8, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess && T_out) ce = cudaMemcpyAsync(T_out, d_T, (size_t)n_cells * 8, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess && status)
+        ce = cudaMemcpyAsync(status, d_st, (size_t)n_cells * 4, cudaMemcpyDeviceToHost, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "device-to-host copy");
+    ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "synchronising the step");
+    return CHEM_OK;
+}
+
+int chem_state_from_tpy(chem_handle_t hh, int64_t n, int64_t ld, const double *T, const double *P,
+                        const double *Y, double *rho_s, double *e, void *stream) {
+    Handle *h = hh;
+    if (!h || !T || !P || !Y || !rho_s || !e) return fail(CHEM_E_INVALID_ARG, "NULL argument");
+    if (n < 0 || (ld != 0 && ld < n)) return fail(CHEM_E_INVALID_ARG, "sizes");
+    if (n == 0) return CHEM_OK;
+    if (ld == 0) ld = n;
+    const int bs = 128;
+    state_from_tpy_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, (cudaStream_t)stream>>>(h->mech, n, ld, T, P, Y,
+                                                                                          rho_s, e);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(ce, "state_from_tpy launch");
+    h->launches.fetch_add(1);
+    return CHEM_OK;
+}
+
+int chem_temperature(chem_handle_t hh, int64_t n, int64_t ld, const double *rho_s, const double *e,
+                     const double *T_guess, double *T_out, void *stream) {
+    Handle *h = hh;
+    if (!h || !rho_s || !e || !T_out) return fail(CHEM_E_INVALID_ARG, "NULL argument");
+    if (n < 0 || (ld != 0 && ld < n)) return fail(CHEM_E_INVALID_ARG, "sizes");
+    if (n == 0) return CHEM_OK;
+    if (ld == 0) ld = n;
+    const int bs = 128;
+    temperature_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, (cudaStream_t)stream>>>(h->mech, n, ld, rho_s, e,
+                                                                                      T_guess, T_out);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(ce, "temperature launch");
+    h->launches.fetch_add(1);
+    return CHEM_OK;
+}
+
+int chem_get_lanes_per_cell(chem_handle_t hh, int32_t precision, int32_t *lanes) {
+    Handle *h = hh;
+    if (!h || !lanes || (precision != CHEM_FP64 && precision != CHEM_MIXED))
+        return fail(CHEM_E_INVALID_ARG, "bad argument");
+    *lanes = h->lanes[precision];
+    return CHEM_OK;
+}
+
+int chem_launch_count(chem_handle_t hh, int64_t *count) {
+    Handle *h = hh;
+    if (!h || !count) return fail(CHEM_E_INVALID_ARG, "bad argument");
+    *count = h->launches.load();
+    return CHEM_OK;
+}
+
+const char *chem_strerror(int code) {
+    switch (code) {
+        case CHEM_OK: return "ok";
+        case CHEM_E_INVALID_ARG: return "invalid argument";
+        case CHEM_E_BAD_MECHANISM: return "invalid mechanism";
+        case CHEM_E_OOM: return "out of memory";
+        case CHEM_E_OVER_BUDGET: return "request exceeds the HBM budget";
+        case CHEM_E_CUDA: return "CUDA error";
+        case CHEM_E_TIMEOUT: return "timed out";
+        case CHEM_E_UNSUPPORTED: return "size beyond the kernels' limits";
+        case CHEM_E_NOT_FOUND: return "unknown ticket";
+        default: return "unknown error code";
+    }
+}
+
+const char *chem_last_error_message(void) { return g_errmsg; }
+
+}  // extern "C"
