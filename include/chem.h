@@ -146,6 +146,27 @@ int chem_advance_ex(chem_handle_t h, const chem_advance_args *a);
 int chem_advance_host(chem_handle_t h, int64_t n_cells, int64_t ld, double *rho_s, double *e,
                       double dt, double *T_out, int32_t *status);
 
+/* No counterpart in the paper: an allocation-free chem_advance_host for
+ * callers that must not allocate device memory while running (a host flow
+ * solver inside a framework that owns the device through its own memory
+ * pool, or a real-time loop that forbids cudaMalloc/cudaFree after start-up).
+ * Same arguments and results as chem_advance_host, but the device staging of
+ * rho_s, e, T_out, status and the kernel's work counter lives in one fixed
+ * 16 MiB file-scope device array (chem_static_scratch_bytes reports the
+ * size) that every GPU loading the library keeps until exit; nothing is
+ * allocated per call.  A request needing more than the array -- about
+ * 16 MiB / (8 N_s + 20) cells -- returns CHEM_E_UNSUPPORTED with the cell
+ * limit in chem_last_error_message; split it.  The first call on a device
+ * looks up the array's device address (once per device, the handle's device
+ * must be current).  All calls share the array and it keeps the last call's
+ * contents; calls are serialised per device inside one process, and calls
+ * that overlapped on the GPU would race.  Synchronous. */
+int chem_advance_host_static(chem_handle_t h, int64_t n_cells, int64_t ld, double *rho_s,
+                             double *e, double dt, double *T_out, int32_t *status);
+
+/* Size in bytes of chem_advance_host_static's static device array. */
+int chem_static_scratch_bytes(int64_t *bytes);
+
 /* Initial states from temperature T [n], pressure P [n] (Pa) and mass
  * fractions Y [N_s*ld] (all device): rho = P / (R T sum_s Y_s/M_s) (Dalton's
  * law, Eq. 5), rho_s = rho Y_s, e from Eq. 3.  Asynchronous on `stream`. */

@@ -69,6 +69,8 @@ def lib():
             "chem_advance": [p, i64, p, p, d, p],
             "chem_advance_ex": [p, p],
             "chem_advance_host": [p, i64, i64, p, p, d, p, p],
+            "chem_advance_host_static": [p, i64, i64, p, p, d, p, p],
+            "chem_static_scratch_bytes": [p],
             "chem_state_from_tpy": [p, i64, i64, p, p, p, p, p, p],
             "chem_temperature": [p, i64, i64, p, p, p, p, p],
             "chem_get_lanes_per_cell": [p, i32, p],
@@ -166,6 +168,15 @@ class Chem:
         check(lib().chem_advance_host(self.h, n, rho.shape[1], rho.ctypes.data, e.ctypes.data,
                                       float(dt), None if T_out is None else T_out.ctypes.data,
                                       None if status is None else status.ctypes.data))
+
+    def advance_host_static(self, rho, e, dt, T_out=None, status=None):
+        """Like advance_host, but staged in the library's fixed device array:
+        no device allocation per call; raises ChemError(UNSUPPORTED) when the
+        request does not fit."""
+        n = e.shape[0]
+        check(lib().chem_advance_host_static(self.h, n, rho.shape[1], rho.ctypes.data, e.ctypes.data,
+                                             float(dt), None if T_out is None else T_out.ctypes.data,
+                                             None if status is None else status.ctypes.data))
 
     def state_from_tpy(self, T, P, Y, rho, e, stream=None):
         n = int(T.shape[0])
