@@ -33,11 +33,14 @@ WORKLOAD_DESC = ("synthetic 36 sp / 308 rxn mechanism (4 elements, 40 third-body
                  "adaptive substeps")
 EXP_FLOPS = 40          # one FP64 exp occupies the FP64 pipe like ~20 DFMA (measured)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 x max clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FFMA/clk x 2 x max clock
 
 
 def work_model(mech):
-    """Algorithmic FP64 flops of one Newton iteration of one cell (FMA = 2,
-    exp = EXP_FLOPS), from the mechanism's structure."""
+    """Algorithmic flops of one Newton iteration of one cell (FMA = 2, exp =
+    EXP_FLOPS), from the mechanism's structure, split into the parts the
+    mixed-precision path keeps in FP64 and the Jacobian/LU parts it moves to
+    FP32 (all of it is FP64 on the FP64 path)."""
     ns, nr = mech.ns, mech.nr
     n = ns + 1
     nu = np.zeros((nr, ns), np.int64)
@@ -58,13 +61,18 @@ def work_model(mech):
         sp_ent += rows
     thermo = 38 * ns
     t_recovery = 2 * 27 * ns
-    rates = 40 * nr + 8 * nD + 2 * nr * EXP_FLOPS
-    gathers = 6 * sp_ent + 6 * ns
+    rates_src = 30 * nr + 2 * nr * EXP_FLOPS     # rate constants, progress rates
+    rates_jac = 10 * nr                          # C_M K_f, C_M K_b, dQ/dT
+    d_entries = 8 * nD
+    gather_src = 2 * sp_ent + 2 * ns
+    gather_jac = 4 * sp_ent + 4 * ns
     jac = 6 * ns * n + 2 * j_ent + 2 * nD + 6 * n
     lu = sum(2 * (n - j - 1) * (n - j) + (n - j - 1) + 1 for j in range(n)) + n * n
-    update = 6 * n
-    total = thermo + t_recovery + rates + gathers + jac + lu + update
-    return dict(flops=total, exp=2 * nr, nD=nD, j_ent=j_ent, lu=lu, rates=rates, jac=jac)
+    update = 9 * n
+    fp64_core = thermo + t_recovery + rates_src + gather_src + update
+    jac_part = rates_jac + d_entries + gather_jac + jac + lu
+    return dict(flops=fp64_core + jac_part, mixed_fp64=fp64_core, mixed_fp32=jac_part,
+                exp=2 * nr, nD=nD, j_ent=j_ent, lu=lu)
 
 
 class Clocks:
@@ -231,7 +239,10 @@ def main():
     ap.add_argument("--ref-cells", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
+                    help="both: time FP64 and mixed, headline = mixed")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per cell (0: the library's choice)")
+    ap.add_argument("--workload", default=WORKLOAD, help="named workload of synth.workload")
     ap.add_argument("--cells", type=int, default=0,
                     help="time the first CELLS cells only (a smaller case for profiling)")
     args = ap.parse_args()
@@ -248,54 +259,80 @@ def main():
 
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
-    mech, f, dt = synth.workload(WORKLOAD)
+    mech, f, dt = synth.workload(args.workload)
     if args.cells:
         f = synth.subsample(f, np.arange(min(args.cells, f.n)))
     wm = work_model(mech)
-    ch = chem.Chem(mech)
     stream = torch.cuda.Stream(device)
+    handles = {}
+    for name, prec in (("fp64", chem.FP64), ("mixed", chem.MIXED)):
+        if args.precision in ("both", name):
+            handles[name] = chem.Chem(mech, lanes_per_cell=args.lanes, precision=prec)
+    head_name = "mixed" if "mixed" in handles else "fp64"
+    head = handles[head_name]
     with torch.cuda.stream(stream):
         T = torch.tensor(f.T, device=device)
         Pp = torch.tensor(f.P, device=device)
         Y = torch.tensor(f.Y, device=device)
         rho0 = torch.empty_like(Y)
         e0 = torch.empty_like(T)
-        ch.state_from_tpy(T, Pp, Y, rho0, e0, stream=stream)
+        head.state_from_tpy(T, Pp, Y, rho0, e0, stream=stream)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
     stream.synchronize()
     n = f.n
-    prec = chem.FP64 if args.precision == "fp64" else chem.MIXED
 
-    # stats run (untimed) for the work model: Newton iterations per launch
-    _, _, stats = time_path(torch, ch, rho0, e0, T, dt, prec, 1, 0, flush, stream, True)
-
-    launches0 = ch.launch_count()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        t0 = time.perf_counter()
-        tot, ker, _ = time_path(torch, ch, rho0, e0, T, dt, prec, args.steps, args.warmup, flush,
-                                stream, False)
+    results = {}
+    clk = None
+    gpu_launches = 0
+    wall = 0.0
+    for name, ch in handles.items():
+        prec = chem.MIXED if name == "mixed" else chem.FP64
+        # untimed statistics launch: Newton iterations for the work model
+        _, _, stats = time_path(torch, ch, rho0, e0, T, dt, prec, 1, 0, flush, stream, True)
+        launches0 = ch.launch_count()
+        if world > 1:
+            torch.distributed.barrier()
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    launches = ch.launch_count() - launches0
-    gpu_launches = launches * args.steps // (args.steps + args.warmup)
-    step_ms = barrier_max(world, statistics.mean(tot), device)
-    kern_ms = barrier_max(world, statistics.mean(ker), device)
-    value = world * n / (step_ms * 1e-3)
-
-    flops_launch = stats["newton_iters"] * wm["flops"]
-    achieved = flops_launch / (kern_ms * 1e-3) / 1e12
-    bytes_launch = n * (16 * (mech.ns + 1) + 8)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "chem::be_kernel<%d,double>" % ch.lanes(prec),
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe); "
-                               "probe measured 1.193 TFLOP/s",
-                "work_model": "%d FP64 flop per Newton iteration (exp counted as %d), %d Newton "
-                              "iterations per launch" % (wm["flops"], EXP_FLOPS, stats["newton_iters"]),
+        with Clocks(local) as ck:
+            t0 = time.perf_counter()
+            tot, ker, _ = time_path(torch, ch, rho0, e0, T, dt, prec, args.steps, args.warmup, flush,
+                                    stream, False)
+            torch.cuda.synchronize()
+            w = time.perf_counter() - t0
+        launches = (ch.launch_count() - launches0) * args.steps // (args.steps + args.warmup)
+        step_ms = barrier_max(world, statistics.mean(tot), device)
+        kern_ms = barrier_max(world, statistics.mean(ker), device)
+        it = stats["newton_iters"]
+        if name == "fp64":
+            a64 = it * wm["flops"] / (kern_ms * 1e-3) / 1e12
+            a32 = 0.0
+        else:
+            a64 = it * wm["mixed_fp64"] / (kern_ms * 1e-3) / 1e12
+            a32 = it * wm["mixed_fp32"] / (kern_ms * 1e-3) / 1e12
+        bytes_launch = n * (16 * (mech.ns + 1) + 8)
+        roof = {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": a64 / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "chem::be_kernel<%d,%s>" % (ch.lanes(prec), "double" if name == "fp64" else "float"),
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe, the "
+                               "binding pipe); probe measured 1.193 TFLOP/s",
+                "work_model": "%d FP64 flop per Newton iteration%s (exp counted as %d), %d Newton "
+                              "iterations per launch" % (
+                                  wm["flops"] if name == "fp64" else wm["mixed_fp64"],
+                                  "" if name == "fp64" else " plus %d FP32 flop" % wm["mixed_fp32"],
+                                  EXP_FLOPS, it),
                 "hbm_gbs": bytes_launch / (kern_ms * 1e-3) / 1e9}
+        if name == "mixed":
+            roof["fp32_achieved"] = a32
+            roof["fp32_peak"] = FP32_PEAK_TFLOPS
+        results[name] = dict(value=world * n / (step_ms * 1e-3), ms_per_step=step_ms,
+                             kernel_ms_per_step=kern_ms, lanes_per_cell=ch.lanes(prec),
+                             newton_iters_mean=stats["newton_iters_mean"],
+                             newton_iters_max=stats["newton_iters_max"],
+                             cells_ok=stats["status_ok"], roofline=roof)
+        if ch is head:
+            clk = ck.summary()
+            gpu_launches = launches
+            wall = w
 
     e2e = None
     if not args.no_e2e:
@@ -308,7 +345,7 @@ def main():
             rho_h[...] = rho_src
             e_h[...] = e_src
             t1 = time.perf_counter()
-            ch.advance_host(rho_h, e_h, dt)
+            head.advance_host(rho_h, e_h, dt)
             t2 = time.perf_counter()
             if i >= 1:
                 times.append(t2 - t1)
@@ -316,7 +353,8 @@ def main():
         e2e = {"value": world * n / e2e_s, "unit": "cell-updates/s",
                "h2d_bytes_per_step": int(n * (mech.ns + 1) * 8),
                "d2h_bytes_per_step": int(n * (mech.ns + 1) * 8),
-               "api": "chem_advance_host (pinned host buffers, synchronous)", "steps": len(times)}
+               "api": "chem_advance_host (pinned host buffers, synchronous), %s" % head_name,
+               "steps": len(times)}
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -324,24 +362,30 @@ def main():
         cb.pop("newton_iters_mean", None)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        hr = results[head_name]
+        line = {"metric": METRIC, "value": hr["value"], "unit": "cell-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": hr["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if prec == chem.FP64 else "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD_DESC if not args.cells else
-                           "first %d cells of: %s" % (n, WORKLOAD_DESC),
-                           "cells": n, "precision": args.precision,
-                           "lanes_per_cell": ch.lanes(prec),
+                "dtype": "f64" if head_name == "fp64" else "f32+f64", "data": "synthetic",
+                "config": {"workload": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload)
+                           if not args.cells else "first %d cells of: %s" % (n, args.workload),
+                           "cells": n, "precision": head_name,
+                           "lanes_per_cell": hr["lanes_per_cell"],
                            "l2": "flushed (256 MiB write) before every step; state restored from "
                                  "a device copy inside the step",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "kernel_ms_per_step": kern_ms, "wall_s": wall,
-                "newton_iters_mean": stats["newton_iters_mean"],
-                "newton_iters_max": stats["newton_iters_max"], "cells_ok": stats["status_ok"],
-                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
-                "gpu_launches": gpu_launches, "clocks": clk.summary()}
+                "kernel_ms_per_step": hr["kernel_ms_per_step"], "wall_s": wall,
+                "newton_iters_mean": hr["newton_iters_mean"],
+                "newton_iters_max": hr["newton_iters_max"], "cells_ok": hr["cells_ok"],
+                "roofline": hr["roofline"], "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": gpu_launches, "clocks": clk}
+        for name, r in results.items():
+            line[name] = {k: v for k, v in r.items()}
+        if "fp64" in results and "mixed" in results:
+            line["mixed_over_fp64"] = results["mixed"]["value"] / results["fp64"]["value"]
         print(json.dumps(line), flush=True)
-    ch.close()
+    for ch in handles.values():
+        ch.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -96,11 +96,14 @@ typedef struct chem_options {
     int32_t lanes_per_cell;   /* 0 = chosen by the library; else 1,2,4,8,16,32 */
     int32_t autotune;         /* 1: time the lane choices once and keep the best */
     int64_t hbm_budget_bytes; /* serving: device bytes requests may hold (0 = 50% of free) */
+    int32_t max_newton_mixed; /* Newton iterations per attempt on the CHEM_MIXED path, whose
+                                 FP32 LU makes convergence linear; 1..1000 */
 } chem_options;
 
 /* Fills *o with the defaults: FP64, rtol 1e-10, atol_rel 1e-12,
  * max_newton 12, max_halvings 20, max_attempts 1000, point_implicit 0,
- * div_check 1, lanes_per_cell 0, autotune 0, hbm_budget_bytes 0. */
+ * div_check 1, lanes_per_cell 0, autotune 0, hbm_budget_bytes 0,
+ * max_newton_mixed 30. */
 int chem_default_options(chem_options *o);
 
 /* Validates the mechanism (index ranges, 1..3 species per side with

@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("max_newton", C.c_int32), ("max_halvings", C.c_int32), ("max_attempts", C.c_int32),
                 ("point_implicit", C.c_int32), ("div_check", C.c_int32),
                 ("lanes_per_cell", C.c_int32), ("autotune", C.c_int32),
-                ("hbm_budget_bytes", C.c_int64)]
+                ("hbm_budget_bytes", C.c_int64), ("max_newton_mixed", C.c_int32)]
 
 
 class AdvanceArgs(C.Structure):

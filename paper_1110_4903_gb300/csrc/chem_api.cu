@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -22,7 +23,6 @@ namespace chem {
 
 const void *be_kernel_fp64(int G);
 const void *be_kernel_mixed(int G);
-long long slot_bytes_host(int ns, int nr, int nD, int jt);
 
 static thread_local char g_errmsg[512] = "";
 
@@ -120,13 +120,15 @@ static int validate(const chem_mech_desc *d) {
 
 // Derived tables (layouts in chem_internal.h)
 struct HostTables {
-    std::vector<double> thermo, tmid, sp, rxn_d, deff, dEf;
-    std::vector<int> rxn_i, dcol, sp_ptr, sp_ent, jmap, j_ptr, j_ent, col_ptr, col_ent;
-    int nD = 0, nnz = 0;
+    std::vector<double> thermo, tmid, sp, rxn_d, eff_c, d_c, j_c, sp_nu, exp_tab;
+    std::vector<float> rxn_df, d_cf, j_cf, sp_nuf;
+    std::vector<int> rxn_f, eff_ptr, eff_sp, d_i0, d_i1, j_sk, j_ptr, j_d, it_ptr, sp_item_ptr, sp_r;
+    int nD = 0, nD_F = 0, nD_B = 0, nD_FB = 0, nJ = 0, n_items = 0;
 };
 
 static void build_tables(const chem_mech_desc *d, HostTables &t) {
     const int ns = d->n_species, nr = d->n_reactions;
+    const int SENT = ns;   // sentinel species index
     t.thermo.assign((size_t)ns * 2 * kThermoStride, 0.0);
     t.tmid.assign(d->t_mid, d->t_mid + ns);
     t.sp.assign((size_t)ns * kSpStride, 0.0);
@@ -156,115 +158,166 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         t.sp[s * kSpStride + 2] = kR / M;
         t.sp[s * kSpStride + 3] = ef[s];
     }
-    // dense net stoichiometry
+    // dense stoichiometry
     std::vector<int> nuR((size_t)nr * ns, 0), nuP((size_t)nr * ns, 0);
     for (int r = 0; r < nr; ++r)
         for (int j = 0; j < 3; ++j) {
             if (d->reac_sp[r * 3 + j] >= 0) nuR[(size_t)r * ns + d->reac_sp[r * 3 + j]] += d->reac_nu[r * 3 + j];
             if (d->prod_sp[r * 3 + j] >= 0) nuP[(size_t)r * ns + d->prod_sp[r * 3 + j]] += d->prod_nu[r * 3 + j];
         }
+    auto net = [&](int r, int s) { return nuP[(size_t)r * ns + s] - nuR[(size_t)r * ns + s]; };
+    // per reaction: rate constants and concentration factors with repetition
     t.rxn_d.assign((size_t)nr * kRxnDStride, 0.0);
-    t.rxn_i.assign((size_t)nr * kRxnIStride, -1);
-    std::vector<int> drxn;   // reaction of each D entry
+    t.rxn_f.assign((size_t)nr * kRxnFStride, 0);
+    t.eff_ptr.assign(nr + 1, 0);
+    std::vector<std::array<int, 3>> facR(nr), facP(nr);
     for (int r = 0; r < nr; ++r) {
         const int tb = d->third_body[r];
         int order = tb, dnu = 0;
-        double Ef = 0.0;
         for (int j = 0; j < 3; ++j)
             if (d->reac_sp[r * 3 + j] >= 0) order += d->reac_nu[r * 3 + j];
-        for (int s = 0; s < ns; ++s) {
-            const int v = nuP[(size_t)r * ns + s] - nuR[(size_t)r * ns + s];
-            dnu += v;
-            Ef += v * d->molar_mass[s] * ef[s];
-        }
+        for (int s = 0; s < ns; ++s) dnu += net(r, s);
         const double A = d->arr_A[r];
         double *rd = &t.rxn_d[(size_t)r * kRxnDStride];
         rd[0] = A > 0 ? std::log(A) + (order - 1) * std::log(1e-6) : -INFINITY;
         rd[1] = d->arr_beta[r];
         rd[2] = d->arr_Ea[r] / kR;
         rd[3] = (double)dnu;
-        rd[4] = Ef;
-        int *ri = &t.rxn_i[(size_t)r * kRxnIStride];
-        int nupack = 0;
+        std::array<int, 3> fr{SENT, SENT, SENT}, fp{SENT, SENT, SENT};
+        int nf = 0, nb = 0;
         for (int j = 0; j < 3; ++j) {
-            ri[j] = d->reac_sp[r * 3 + j];
-            ri[3 + j] = d->prod_sp[r * 3 + j];
-            if (ri[j] >= 0) nupack |= d->reac_nu[r * 3 + j] << (2 * j);
-            if (ri[3 + j] >= 0) nupack |= d->prod_nu[r * 3 + j] << (8 + 2 * j);
+            if (d->reac_sp[r * 3 + j] >= 0)
+                for (int q = 0; q < d->reac_nu[r * 3 + j]; ++q) fr[nf++] = d->reac_sp[r * 3 + j];
+            if (d->prod_sp[r * 3 + j] >= 0)
+                for (int q = 0; q < d->prod_nu[r * 3 + j]; ++q) fp[nb++] = d->prod_sp[r * 3 + j];
         }
-        ri[6] = nupack;
-        // D columns: reactant species, product species, then efficiency species
-        std::vector<int> cols;
-        std::map<int, std::pair<int, int>> slots;   // species -> (rsl, psl)
-        for (int j = 0; j < 3; ++j) {
-            const int s = d->reac_sp[r * 3 + j];
-            if (s < 0) continue;
-            if (!slots.count(s)) { slots[s] = {3, 3}; cols.push_back(s); }
-            slots[s].first = j;
-        }
-        for (int j = 0; j < 3; ++j) {
-            const int s = d->prod_sp[r * 3 + j];
-            if (s < 0) continue;
-            if (!slots.count(s)) { slots[s] = {3, 3}; cols.push_back(s); }
-            slots[s].second = j;
-        }
+        facR[r] = fr;
+        facP[r] = fp;
+        t.rxn_f[2 * r] = fr[0] | (fr[1] << 8) | (fr[2] << 16) | ((tb & 1) << 24);
+        t.rxn_f[2 * r + 1] = fp[0] | (fp[1] << 8) | (fp[2] << 16);
         if (tb && d->tb_eff)
-            for (int s = 0; s < ns; ++s)
-                if (d->tb_eff[(size_t)r * ns + s] != 1.0 && !slots.count(s)) {
-                    slots[s] = {3, 3};
-                    cols.push_back(s);
+            for (int s = 0; s < ns; ++s) {
+                const double a = d->tb_eff[(size_t)r * ns + s];
+                if (a != 1.0) {
+                    t.eff_sp.push_back(s);
+                    t.eff_c.push_back(a - 1.0);
                 }
-        const int doff = t.nD;
-        for (int s : cols) {
-            const auto sl = slots[s];
-            t.dcol.push_back(s | (sl.first << 8) | (sl.second << 10));
-            t.deff.push_back(tb ? (d->tb_eff ? d->tb_eff[(size_t)r * ns + s] : 1.0) - 1.0 : 0.0);
-            t.dEf.push_back(Ef);
-            drxn.push_back(r);
-            ++t.nD;
-        }
-        ri[7] = (tb & 1) | (doff << 1) | ((int)cols.size() << 21);
+            }
+        t.eff_ptr[r + 1] = (int)t.eff_sp.size();
     }
-    // species CSR: reactions with nonzero net coefficient
-    t.sp_ptr.assign(ns + 1, 0);
-    for (int s = 0; s < ns; ++s) {
-        for (int r = 0; r < nr; ++r) {
-            const int v = nuP[(size_t)r * ns + s] - nuR[(size_t)r * ns + s];
-            if (v != 0) t.sp_ent.push_back((r << 8) | (v & 0xff));
+    // D entries: (reaction, column species) pairs, grouped by kind
+    struct DEnt { int r, k, grp; int fa, fb, ba, bb; double cf, cb, ce; };
+    std::vector<DEnt> ents;
+    for (int r = 0; r < nr; ++r) {
+        std::vector<int> cols;
+        auto addc = [&](int s) { if (std::find(cols.begin(), cols.end(), s) == cols.end()) cols.push_back(s); };
+        for (int j = 0; j < 3; ++j) if (d->reac_sp[r * 3 + j] >= 0) addc(d->reac_sp[r * 3 + j]);
+        for (int j = 0; j < 3; ++j) if (d->prod_sp[r * 3 + j] >= 0) addc(d->prod_sp[r * 3 + j]);
+        const int tb = d->third_body[r];
+        if (tb && d->tb_eff)
+            for (int s = 0; s < ns; ++s) if (d->tb_eff[(size_t)r * ns + s] != 1.0) addc(s);
+        for (int k : cols) {
+            DEnt e{};
+            e.r = r;
+            e.k = k;
+            const int vf = nuR[(size_t)r * ns + k], vb = nuP[(size_t)r * ns + k];
+            const double invM = 1.0 / d->molar_mass[k];
+            // remaining factors after removing one occurrence of k
+            auto rest = [&](const std::array<int, 3> &f, int &x, int &y) {
+                int out[3] = {SENT, SENT, SENT}, m = 0;
+                bool removed = false;
+                for (int q = 0; q < 3; ++q) {
+                    if (!removed && f[q] == k) { removed = true; continue; }
+                    if (f[q] != SENT) out[m++] = f[q];
+                }
+                x = out[0];
+                y = out[1];
+            };
+            e.fa = e.fb = e.ba = e.bb = SENT;
+            if (vf > 0) rest(facR[r], e.fa, e.fb);
+            if (vb > 0) rest(facP[r], e.ba, e.bb);
+            e.cf = vf * invM;
+            e.cb = vb * invM;
+            e.ce = (tb ? (d->tb_eff ? d->tb_eff[(size_t)r * ns + k] : 1.0) - 1.0 : 0.0) * invM;
+            e.grp = vf > 0 && vb == 0 ? 0 : (vf == 0 && vb > 0 ? 1 : (vf > 0 ? 2 : 3));
+            ents.push_back(e);
         }
-        t.sp_ptr[s + 1] = (int)t.sp_ent.size();
     }
-    // species-block gather lists: J_sk = M_s sum_r nu_rs D_rk
-    std::vector<std::vector<int>> lists((size_t)ns * ns);
+    std::stable_sort(ents.begin(), ents.end(), [](const DEnt &a, const DEnt &b) { return a.grp < b.grp; });
+    t.nD = (int)ents.size();
+    for (const auto &e : ents) {
+        if (e.grp <= 0) t.nD_F++;
+        if (e.grp <= 1) t.nD_B++;
+        if (e.grp <= 2) t.nD_FB++;
+        t.d_i0.push_back(e.r | (e.k << 16));
+        t.d_i1.push_back(e.fa | (e.fb << 8) | (e.ba << 16) | (e.bb << 24));
+        t.d_c.push_back(e.cf);
+        t.d_c.push_back(e.cb);
+        t.d_c.push_back(e.ce);
+    }
+    // species-block gather lists: -hJ_sk gathers nu_rs M_s D_rk
+    std::vector<std::vector<std::pair<int, double>>> lists((size_t)ns * ns);
     for (int j = 0; j < t.nD; ++j) {
-        const int r = drxn[j], k = t.dcol[j] & 0xff;
+        const int r = ents[j].r, k = ents[j].k;
         for (int s = 0; s < ns; ++s) {
-            const int v = nuP[(size_t)r * ns + s] - nuR[(size_t)r * ns + s];
-            if (v != 0) lists[(size_t)s * ns + k].push_back((j << 8) | (v & 0xff));
+            const int v = net(r, s);
+            if (v != 0) lists[(size_t)s * ns + k].push_back({j, v * d->molar_mass[s]});
         }
     }
-    t.jmap.assign((size_t)ns * ns, -1);
+    std::vector<int> order(ns * ns);
+    for (int i = 0; i < ns * ns; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return lists[a].size() > lists[b].size(); });
+    t.nJ = ns * ns;
     t.j_ptr.push_back(0);
-    for (int idx = 0; idx < ns * ns; ++idx) {
-        if (lists[idx].empty()) continue;
-        t.jmap[idx] = t.nnz++;
-        for (int ent : lists[idx]) t.j_ent.push_back(ent);
-        t.j_ptr.push_back((int)t.j_ent.size());
+    for (int idx : order) {
+        const int s = idx / ns, k = idx % ns;
+        t.j_sk.push_back((s << 8) | k);
+        for (const auto &pr : lists[idx]) {
+            t.j_d.push_back(pr.first);
+            t.j_c.push_back(pr.second);
+        }
+        t.j_ptr.push_back((int)t.j_d.size());
     }
-    // energy-row column lists
-    t.col_ptr.assign(ns + 1, 0);
-    for (int k = 0; k < ns; ++k) {
-        for (int j = 0; j < t.nD; ++j)
-            if ((t.dcol[j] & 0xff) == k) t.col_ent.push_back(j);
-        t.col_ptr[k + 1] = (int)t.col_ent.size();
+    // species lists (reactions with nu_rs != 0) in chunks of kChunk
+    t.sp_item_ptr.assign(ns + 1, 0);
+    t.it_ptr.push_back(0);
+    for (int s = 0; s < ns; ++s) {
+        int cnt = 0;
+        for (int r = 0; r < nr; ++r) {
+            const int v = net(r, s);
+            if (v == 0) continue;
+            t.sp_r.push_back(r);
+            t.sp_nu.push_back((double)v);
+            if (++cnt == kChunk) {
+                t.it_ptr.push_back((int)t.sp_r.size());
+                cnt = 0;
+            }
+        }
+        if (cnt > 0) t.it_ptr.push_back((int)t.sp_r.size());
+        t.sp_item_ptr[s + 1] = (int)t.it_ptr.size() - 1;
     }
+    t.n_items = (int)t.it_ptr.size() - 1;
+    // 2^(j/64), from the exponential of the exact arguments in long double
+    t.exp_tab.resize(kExpTab);
+    for (int j = 0; j < kExpTab; ++j) t.exp_tab[j] = (double)std::exp2l((long double)j / kExpTab);
+    // FP32 copies for the mixed-precision Jacobian
+    t.rxn_df.assign((size_t)nr * kRxnDStride, 0.0f);
+    for (int r = 0; r < nr; ++r) {
+        t.rxn_df[(size_t)r * kRxnDStride + 0] = (float)t.rxn_d[(size_t)r * kRxnDStride + 1];
+        t.rxn_df[(size_t)r * kRxnDStride + 1] = (float)t.rxn_d[(size_t)r * kRxnDStride + 2];
+        t.rxn_df[(size_t)r * kRxnDStride + 2] = (float)t.rxn_d[(size_t)r * kRxnDStride + 3];
+    }
+    for (double v : t.d_c) t.d_cf.push_back((float)v);
+    for (double v : t.j_c) t.j_cf.push_back((float)v);
+    for (double v : t.sp_nu) t.sp_nuf.push_back((float)v);
     // keep every array non-empty so device pointers are valid
-    if (t.nD == 0) { t.dcol.push_back(0); t.deff.push_back(0); t.dEf.push_back(0); }
-    if (t.sp_ent.empty()) t.sp_ent.push_back(0);
-    if (t.j_ent.empty()) t.j_ent.push_back(0);
-    if (t.col_ent.empty()) t.col_ent.push_back(0);
-    if (t.rxn_d.empty()) t.rxn_d.assign(kRxnDStride, 0.0);
-    if (t.rxn_i.empty()) t.rxn_i.assign(kRxnIStride, -1);
+    auto pad_f = [](std::vector<float> &v) { if (v.empty()) v.push_back(0.0f); };
+    pad_f(t.rxn_df); pad_f(t.d_cf); pad_f(t.j_cf); pad_f(t.sp_nuf);
+    auto pad_i = [](std::vector<int> &v) { if (v.empty()) v.push_back(0); };
+    auto pad_d = [](std::vector<double> &v) { if (v.empty()) v.push_back(0.0); };
+    pad_i(t.eff_sp); pad_d(t.eff_c); pad_i(t.d_i0); pad_i(t.d_i1); pad_d(t.d_c);
+    pad_i(t.j_d); pad_d(t.j_c); pad_i(t.sp_r); pad_d(t.sp_nu); pad_i(t.rxn_f); pad_d(t.rxn_d);
 }
 
 // Copies the tables into one device allocation.
@@ -278,21 +331,14 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
         total += bytes;
         return parts.size() - 1;
     };
-    const size_t i_th = add(t.thermo.data(), t.thermo.size() * 8);
-    const size_t i_tm = add(t.tmid.data(), t.tmid.size() * 8);
-    const size_t i_sp = add(t.sp.data(), t.sp.size() * 8);
-    const size_t i_rd = add(t.rxn_d.data(), t.rxn_d.size() * 8);
-    const size_t i_ri = add(t.rxn_i.data(), t.rxn_i.size() * 4);
-    const size_t i_dc = add(t.dcol.data(), t.dcol.size() * 4);
-    const size_t i_de = add(t.deff.data(), t.deff.size() * 8);
-    const size_t i_dE = add(t.dEf.data(), t.dEf.size() * 8);
-    const size_t i_spp = add(t.sp_ptr.data(), t.sp_ptr.size() * 4);
-    const size_t i_spe = add(t.sp_ent.data(), t.sp_ent.size() * 4);
-    const size_t i_jm = add(t.jmap.data(), t.jmap.size() * 4);
-    const size_t i_jp = add(t.j_ptr.data(), t.j_ptr.size() * 4);
-    const size_t i_je = add(t.j_ent.data(), t.j_ent.size() * 4);
-    const size_t i_cp = add(t.col_ptr.data(), t.col_ptr.size() * 4);
-    const size_t i_ce = add(t.col_ent.data(), t.col_ent.size() * 4);
+    auto addv = [&](const auto &v) { return add(v.data(), v.size() * sizeof(v[0])); };
+    const size_t i_th = addv(t.thermo), i_tm = addv(t.tmid), i_sp = addv(t.sp), i_rd = addv(t.rxn_d),
+                 i_rf = addv(t.rxn_f), i_ep = addv(t.eff_ptr), i_es = addv(t.eff_sp), i_ec = addv(t.eff_c),
+                 i_d0 = addv(t.d_i0), i_d1 = addv(t.d_i1), i_dc = addv(t.d_c), i_jsk = addv(t.j_sk),
+                 i_jp = addv(t.j_ptr), i_jd = addv(t.j_d), i_jc = addv(t.j_c), i_itp = addv(t.it_ptr),
+                 i_sip = addv(t.sp_item_ptr), i_spr = addv(t.sp_r), i_spn = addv(t.sp_nu),
+                 i_ex = addv(t.exp_tab), i_rdf = addv(t.rxn_df), i_dcf = addv(t.d_cf),
+                 i_jcf = addv(t.j_cf), i_spnf = addv(t.sp_nuf);
     cudaError_t e = cudaMalloc(&h->dev_tables, total);
     if (e != cudaSuccess) return fail(CHEM_E_OOM, "device tables (%zu bytes): %s", total, cudaGetErrorString(e));
     h->dev_tables_bytes = total;
@@ -301,28 +347,40 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     e = cudaMemcpy(h->dev_tables, staging.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "copying mechanism tables");
     char *b = static_cast<char *>(h->dev_tables);
+    auto at = [&](size_t i) { return (const void *)(b + parts[i].off); };
     DeviceMech &m = h->mech;
     m.ns = ns;
     m.nr = nr;
     m.nD = t.nD;
-    m.nnz = t.nnz;
-    m.nsp_ent = (int)t.sp_ent.size();
-    m.ncol_ent = (int)t.col_ent.size();
-    m.thermo = (const double *)(b + parts[i_th].off);
-    m.tmid = (const double *)(b + parts[i_tm].off);
-    m.sp = (const double *)(b + parts[i_sp].off);
-    m.rxn_d = (const double *)(b + parts[i_rd].off);
-    m.rxn_i = (const int *)(b + parts[i_ri].off);
-    m.dcol = (const int *)(b + parts[i_dc].off);
-    m.deff = (const double *)(b + parts[i_de].off);
-    m.dEf = (const double *)(b + parts[i_dE].off);
-    m.sp_ptr = (const int *)(b + parts[i_spp].off);
-    m.sp_ent = (const int *)(b + parts[i_spe].off);
-    m.jmap = (const int *)(b + parts[i_jm].off);
-    m.j_ptr = (const int *)(b + parts[i_jp].off);
-    m.j_ent = (const int *)(b + parts[i_je].off);
-    m.col_ptr = (const int *)(b + parts[i_cp].off);
-    m.col_ent = (const int *)(b + parts[i_ce].off);
+    m.nD_F = t.nD_F;
+    m.nD_B = t.nD_B;
+    m.nD_FB = t.nD_FB;
+    m.nJ = t.nJ;
+    m.n_items = t.n_items;
+    m.thermo = (const double *)at(i_th);
+    m.tmid = (const double *)at(i_tm);
+    m.sp = (const double *)at(i_sp);
+    m.rxn_d = (const double *)at(i_rd);
+    m.rxn_f = (const int *)at(i_rf);
+    m.eff_ptr = (const int *)at(i_ep);
+    m.eff_sp = (const int *)at(i_es);
+    m.eff_c = (const double *)at(i_ec);
+    m.d_i0 = (const int *)at(i_d0);
+    m.d_i1 = (const int *)at(i_d1);
+    m.d_c = (const double *)at(i_dc);
+    m.j_sk = (const int *)at(i_jsk);
+    m.j_ptr = (const int *)at(i_jp);
+    m.j_d = (const int *)at(i_jd);
+    m.j_c = (const double *)at(i_jc);
+    m.it_ptr = (const int *)at(i_itp);
+    m.sp_item_ptr = (const int *)at(i_sip);
+    m.sp_r = (const int *)at(i_spr);
+    m.sp_nu = (const double *)at(i_spn);
+    m.exp_tab = (const double *)at(i_ex);
+    m.rxn_df = (const float *)at(i_rdf);
+    m.d_cf = (const float *)at(i_dcf);
+    m.j_cf = (const float *)at(i_jcf);
+    m.sp_nuf = (const float *)at(i_spnf);
     return CHEM_OK;
 }
 
@@ -333,7 +391,7 @@ static int configure(Handle *h, int prec, int G, LaunchCfg &cfg) {
     const void *fn = prec == CHEM_MIXED ? be_kernel_mixed(G) : be_kernel_fp64(G);
     if (!fn) return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d not available", G);
     const int S = 32 / G;
-    const long long sb = slot_bytes_host(h->mech.ns, h->mech.nr, h->mech.nD, prec == CHEM_MIXED ? 4 : 8);
+    const long long sb = slot_bytes_for(h->mech.ns, h->mech.nr, h->mech.nD, h->mech.n_items, prec == CHEM_MIXED ? 4 : 8);
     int best_warps = 0;
     LaunchCfg best{};
     // the attribute is per function and shared by every handle: allow the
@@ -342,7 +400,7 @@ static int configure(Handle *h, int prec, int G, LaunchCfg &cfg) {
                                          (int)h->max_smem_optin);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     for (int wpb : {8, 4, 2, 1}) {
-        const long long smem = (long long)wpb * S * sb;
+        const long long smem = kBlockHeaderBytes + (long long)wpb * S * sb;
         if (smem > h->max_smem_optin) continue;
         int blocks = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, wpb * 32, (size_t)smem);
@@ -452,13 +510,6 @@ __global__ void temperature_kernel(DeviceMech m, long long n, long long ld, cons
     Tout[i] = ok ? T : NAN;
 }
 
-long long slot_bytes_host(int ns, int nr, int nD, int jt) {
-    const int n = ns + 1;
-    long long dbl = 2LL * n + 5LL * ns + 3LL * nr;
-    long long jtn = 3LL * ns + nD + (long long)n * (n + 1);
-    return ((dbl * 8 + jtn * jt) + 15) / 16 * 16;
-}
-
 int launch_step(Handle *h, const chem_advance_args *a, int prec, int G, unsigned long long *counter) {
     LaunchCfg *cfg = nullptr;
     int rc = get_cfg(h, prec, G, &cfg);
@@ -466,8 +517,10 @@ int launch_step(Handle *h, const chem_advance_args *a, int prec, int G, unsigned
     cudaStream_t st = (cudaStream_t)a->stream;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "zeroing the work counter");
-    StepOptions o{h->opts.rtol, h->opts.atol_rel, h->opts.max_newton, h->opts.max_halvings,
-                  h->opts.max_attempts, h->opts.point_implicit, h->opts.div_check};
+    StepOptions o{h->opts.rtol, h->opts.atol_rel,
+                  prec == CHEM_MIXED ? h->opts.max_newton_mixed : h->opts.max_newton,
+                  h->opts.max_halvings, h->opts.max_attempts, h->opts.point_implicit,
+                  h->opts.div_check};
     StepBatch b;
     b.n_cells = a->n_cells;
     b.ld = a->ld > 0 ? a->ld : a->n_cells;
@@ -511,6 +564,7 @@ int chem_default_options(chem_options *o) {
     o->lanes_per_cell = 0;
     o->autotune = 0;
     o->hbm_budget_bytes = 0;
+    o->max_newton_mixed = 30;
     return CHEM_OK;
 }
 
@@ -520,6 +574,8 @@ static int check_options(const chem_options *o) {
     if (!(o->rtol > 0) || !(o->atol_rel >= 0) || !std::isfinite(o->rtol) || !std::isfinite(o->atol_rel))
         return fail(CHEM_E_INVALID_ARG, "tolerances");
     if (o->max_newton < 1 || o->max_newton > 1000) return fail(CHEM_E_INVALID_ARG, "max_newton %d", o->max_newton);
+    if (o->max_newton_mixed < 1 || o->max_newton_mixed > 1000)
+        return fail(CHEM_E_INVALID_ARG, "max_newton_mixed %d", o->max_newton_mixed);
     if (o->max_halvings < 0 || o->max_halvings > 40) return fail(CHEM_E_INVALID_ARG, "max_halvings %d", o->max_halvings);
     if (o->max_attempts < 1 || o->max_attempts > 1000000) return fail(CHEM_E_INVALID_ARG, "max_attempts %d", o->max_attempts);
     const int l = o->lanes_per_cell;

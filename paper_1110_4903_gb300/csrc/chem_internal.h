@@ -3,6 +3,11 @@
 
 #include <cstdint>
 
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+
 namespace chem {
 
 // Physical constants of the CUDA path.
@@ -25,36 +30,60 @@ constexpr int kThermoStride = 16;
 // Species table row (4 doubles): M, 1/M, R/M, e_f = e_s(T_ref).
 constexpr int kSpStride = 4;
 
-// Reaction table row (8 doubles): ln A_SI, beta, Ea/R, sum nu, Ef_r, 0, 0, 0
-// where Ef_r = sum_s nu_rs M_s e_f,s (formation energy per unit progress).
-constexpr int kRxnDStride = 8;
+// Reaction table row (4 doubles): ln A_SI, beta, Ea/R, sum nu.
+constexpr int kRxnDStride = 4;
 
-// Reaction integer row (8 ints):
-//   0..2 reactant species (-1 unused), 3..5 product species (-1 unused),
-//   6    nu packing: reac nu in bits 0..5 (2 bits each), prod nu in bits 8..13
-//   7    third-body flag (bit 0) | D offset << 1 (bits 1..20) | D count << 21
-constexpr int kRxnIStride = 8;
+// Reaction factor words (2 ints per reaction): the reactant concentration
+// factors of prod_s [X_s]^nu'_s listed with repetition (e.g. 2 O -> O, O),
+// padded with the sentinel species index ns (whose concentration is 1 and
+// whose g/RT and h/RT are 0), 8 bits each in bits 0..23, plus the third-body
+// flag in bit 24; then the product factors the same way.
+constexpr int kRxnFStride = 2;
 
-// D column packing (one per (reaction, species) pair the reaction's rate
-// depends on): species in bits 0..7, reactant slot in bits 8..9 (3 = none),
-// product slot in bits 10..11 (3 = none).
+// Species-gather chunk length (entries per work item).
+constexpr int kChunk = 8;
+
+// Entries of the exp table (2^(j/kExpTab)).
+constexpr int kExpTab = 64;
+
+// D entries: one per (reaction r, species k) pair whose concentration the
+// progress rate Q_r depends on, holding dQ_r/drho_k without the all-ones
+// third-body part.  They are sorted into four groups so each group is one
+// uniform loop: reactant-only, product-only, both sides, efficiency-only.
+//   d_i0 = r | k << 16
+//   d_i1 = fa | fb << 8 | ba << 16 | bb << 24  (the remaining factors of
+//          d(prod c)/dc_k on each side, sentinel ns if none)
+//   d_c  = {nu'_rk / M_k, nu''_rk / M_k, (alpha_rk - 1) / M_k}
 struct DeviceMech {
-    int ns, nr, nD, nnz, nsp_ent, ncol_ent;
-    const double *thermo;     // [ns][2][16]
-    const double *tmid;       // [ns]
-    const double *sp;         // [ns][4]
-    const double *rxn_d;      // [nr][8]
-    const int *rxn_i;         // [nr][8]
-    const int *dcol;          // [nD] packed column descriptor
-    const double *deff;       // [nD] alpha_rk - 1 for +M reactions, else 0
-    const double *dEf;        // [nD] Ef of the entry's reaction
-    const int *sp_ptr;        // [ns+1] CSR: reactions with nu_rs != 0 per species
-    const int *sp_ent;        // (r << 8) | (nu & 0xff)
-    const int *jmap;          // [ns*ns] species-block entry -> gather row, -1 = none
-    const int *j_ptr;         // [nnz+1]
-    const int *j_ent;         // (d_index << 8) | (nu & 0xff)
-    const int *col_ptr;       // [ns+1] D entries per column species (energy row)
-    const int *col_ent;       // D indices
+    int ns, nr;
+    int nD, nD_F, nD_B, nD_FB;  // group ends: [0,F) [F,B) [B,FB) [FB,nD)
+    int nJ;                     // species-block entries (ns*ns)
+    int n_items;                // species-gather work items
+    const double *thermo;       // [ns][2][16]
+    const double *tmid;         // [ns]
+    const double *sp;           // [ns][4]
+    const double *rxn_d;        // [nr][4]
+    const int *rxn_f;           // [nr][2]
+    const int *eff_ptr;         // [nr+1] CSR of efficiency corrections of +M reactions
+    const int *eff_sp;          //        species
+    const double *eff_c;        //        alpha - 1
+    const int *d_i0;            // [nD]
+    const int *d_i1;            // [nD]
+    const double *d_c;          // [nD][3]
+    const int *j_sk;            // [nJ] s << 8 | k, longest gather list first
+    const int *j_ptr;           // [nJ+1]
+    const int *j_d;             // D index of each gather term
+    const double *j_c;          // nu_rs * M_s of each gather term
+    const int *it_ptr;          // [n_items+1] ranges of the species lists
+    const int *sp_item_ptr;     // [ns+1] work items of each species
+    const int *sp_r;            // reactions with nu_rs != 0, per species
+    const double *sp_nu;        // nu_rs
+    const double *exp_tab;      // [kExpTab] 2^(j/kExpTab)
+    // FP32 copies for the mixed-precision Jacobian
+    const float *rxn_df;        // [nr][4] beta, Ea/R, sum nu, 0
+    const float *d_cf;          // [nD][3]
+    const float *j_cf;          // gather coefficients
+    const float *sp_nuf;        // species-list coefficients
 };
 
 struct StepOptions {
@@ -80,13 +109,38 @@ struct StepBatch {
 enum CellStatus { kCellOk = 0, kCellNewtonFailed = 1, kCellTFailed = 2, kCellBadInput = 3,
                   kCellTooManySteps = 4 };
 
-// Shared-memory bytes of one cell slot for a mechanism and Jacobian type size.
-inline long long slot_smem_bytes(int ns, int nr, int nD, int jt_bytes) {
+// Shared memory: a block header (the exp table) then one region per cell slot.
+constexpr int kBlockHeaderBytes = kExpTab * 8;
+
+// The D region of a slot holds the nD D entries (Jacobian type) and, earlier
+// in each Newton iteration, the species-gather partial sums (3 doubles per
+// work item); its size in 8-byte units:
+__host__ __device__ inline int dreg8_for(int nD, int n_items, int jt) {
+    const int a = (nD * jt + 7) / 8, b = 3 * n_items;
+    return a > b ? a : b;
+}
+
+// Bytes of one cell slot, in this order:
+//   doubles  x, x0 (n each); c, hRT, gRT with a sentinel (ns+1 each); es, wd (ns each)
+//   JT       dTdr, w, u (ns each); for FP32 also c and hRT copies (ns+1 each)
+//   D region dreg8 * 8 bytes
+//   union    the per-reaction values Q (double) and dQdT, qtb, A1, A2 (JT),
+//            dead once the D entries exist, and the augmented matrix
+//            n x (n+1) in JT, which is written after that
+__host__ __device__ inline long long slot_small_bytes(int ns, int jt) {
+    const long long cnt = 3LL * ns + (jt == 4 ? 2LL * (ns + 1) : 0);
+    return (cnt * jt + 15) / 16 * 16;
+}
+__host__ __device__ inline long long slot_union_bytes(int ns, int nr, int jt) {
     const int n = ns + 1;
-    long long dbl = 2LL * n + 8LL * ns + 3LL * nr;          // x, x0, species arrays, rates
-    long long jt = (long long)nD + (long long)n * (n + 1);  // D and augmented A
-    long long bytes = dbl * 8 + jt * jt_bytes;
-    return (bytes + 15) / 16 * 16;
+    const long long a = (long long)nr * 8 + 4LL * nr * jt, b = (long long)n * (n + 1) * jt;
+    return ((a > b ? a : b) + 15) / 16 * 16;
+}
+__host__ __device__ inline long long slot_bytes_for(int ns, int nr, int nD, int n_items, int jt) {
+    const int n = ns + 1;
+    const long long dbl = (2LL * n + 3LL * (ns + 1) + 2LL * ns) * 8;
+    const long long dreg = ((long long)dreg8_for(nD, n_items, jt) * 8 + 15) / 16 * 16;
+    return (dbl + 15) / 16 * 16 + slot_small_bytes(ns, jt) + dreg + slot_union_bytes(ns, nr, jt);
 }
 
 }  // namespace chem

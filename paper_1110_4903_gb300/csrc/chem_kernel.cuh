@@ -6,8 +6,16 @@
 // whose cell finishes picks up the next cell from a global work counter
 // between iterations, without stalling the other slots.  Per-cell state,
 // rates, the Jacobian and its LU live in shared memory; HBM only sees the
-// cell state (SoA) on load and store.  FP64 is the binding pipe on this
-// part, so every FP64 phase is spread over the G lanes.
+// cell state (SoA) on load and store.
+//
+// FP64 is the binding pipe on this part (2 DFMA/clk/SM against 128 FFMA), so
+// the iteration is laid out to keep every FP64 warp instruction full: each
+// phase is one loop over a flat, uniform work list (reactions, D entries,
+// Jacobian entries ordered by gather length, fixed-size chunks of the
+// species lists), coefficients are stored as doubles (no int-to-double
+// conversions), the pivot search compares integer keys, reciprocals come
+// from rcp.approx plus Newton steps, and exp is a short table-driven
+// evaluation.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,23 +53,69 @@ struct Grp {
         for (int o = G / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
         return v;
     }
-    // max |value| with the lowest index on ties
-    __device__ __forceinline__ static void argmax(double &v, int &i) {
+    // largest key, lowest index on ties
+    __device__ __forceinline__ static void argmax(unsigned long long &k, int &i) {
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
-            double v2 = __shfl_xor_sync(kFull, v, o);
-            int i2 = __shfl_xor_sync(kFull, i, o);
-            if (v2 > v || (v2 == v && i2 < i)) {
-                v = v2;
+            const unsigned long long k2 = __shfl_xor_sync(kFull, k, o);
+            const int i2 = __shfl_xor_sync(kFull, i, o);
+            if (k2 > k || (k2 == k && i2 < i)) {
+                k = k2;
                 i = i2;
             }
         }
     }
 };
 
-__device__ __forceinline__ double ipow3(double c, int nu) {
-    // c^nu for nu in 0..3
-    return nu == 0 ? 1.0 : (nu == 1 ? c : (nu == 2 ? c * c : c * c * c));
+// |v| as an ordered integer key (NaN maps to 0 so it is never the pivot).
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+    return b > 0x7ff0000000000000ULL ? 0ULL : b;
+}
+__device__ __forceinline__ unsigned long long abs_key(float v) {
+    const unsigned b = __float_as_uint(v) & 0x7fffffffu;
+    // widen to the double key scale (order is all that matters)
+    return b > 0x7f800000u ? 0ULL : ((unsigned long long)b << 29);
+}
+__device__ __forceinline__ bool key_is_inf(unsigned long long k, double) { return k >= 0x7ff0000000000000ULL; }
+__device__ __forceinline__ bool key_is_inf(unsigned long long k, float) {
+    return k >= ((unsigned long long)0x7f800000u << 29);
+}
+
+// Reciprocal: hardware approximation refined by two Newton steps
+// (r <- r + r (1 - a r)), each doubling the correct bits.
+__device__ __forceinline__ double frcp(double a) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+    double e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-a, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ float frcp(float a) { return __frcp_rn(a); }
+
+// exp by the table-driven reduction of P. T. P. Tang, ACM TOMS 15(2), 1989:
+// x = (64 k + j) ln2/64 + r with |r| <= ln2/128, exp(x) = 2^k 2^(j/64) e^r,
+// 2^(j/64) from a 64-entry table and e^r - 1 by its degree-5 Taylor
+// polynomial (truncation below 4e-17 on that interval).  |x| > 700 (and NaN)
+// falls back to the library exp.
+__device__ __forceinline__ double fexp(double x, const double *tab) {
+    if (!(fabs(x) <= 700.0)) return exp(x);
+    const double kShift = 6755399441055744.0;               // 1.5 * 2^52
+    const double t = fma(x, 92.33248261689366, kShift);     // x * 64/ln2, rounded
+    const int n = (int)(unsigned)__double_as_longlong(t);
+    const double nd = t - kShift;
+    double r = fma(nd, -0x1.62e42fefa0000p-7, x);            // ln2/64, high 36 bits
+    r = fma(nd, -0x1.cf79abc9e3b3ap-46, r);                  // ln2/64, low part
+    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    p = fma(r, p, 1.0 / 6.0);
+    p = fma(r, p, 0.5);
+    p = fma(r, p, 1.0);
+    p *= r;                                                  // e^r - 1
+    const double s = tab[n & (kExpTab - 1)];
+    const double y = fma(s, p, s);
+    const long long k = (long long)(n >> 6);
+    return __longlong_as_double(__double_as_longlong(y) + (k << 52));
 }
 
 // NASA-7 evaluations from a 16-double thermo row (layout in chem_internal.h)
@@ -80,7 +134,7 @@ __device__ __forceinline__ const double *thermo_row(const DeviceMech &m, int s, 
 // Temperature recovery from (rho_s, e) for every slot whose `need` is set:
 // Newton on sum_s rho_s e_s^sens(T) = e, safeguarded by bisection on
 // [kTlo, kThi], stop at |dT| <= kTtol T (Eq. 3 with the kinetic energy left to
-// the flux stage).  Uniform across the warp; returns ok per slot.
+// the flux stage).  Uniform across the warp.
 template <int G>
 __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, int sl, bool need,
                                           double guess, double &T_out, bool &ok) {
@@ -92,7 +146,7 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
     const double e = x[ns];
     for (int it = 1; it <= kTmaxIter; ++it) {
         if (!__any_sync(kFull, !done)) break;
-        const double invT = 1.0 / T;
+        const double invT = frcp(T);
         double f = 0.0, fp = 0.0;
         for (int s = sl; s < ns; s += G) {
             const double *th = thermo_row(m, s, T);
@@ -100,10 +154,8 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
             nasa_cp_h(th, T, invT, cpR, hRT);
             const double RM = __ldg(m.sp + s * kSpStride + 2);
             const double ef = __ldg(m.sp + s * kSpStride + 3);
-            const double es = RM * T * (hRT - 1.0) - ef;
-            const double cv = RM * (cpR - 1.0);
-            f += x[s] * es;
-            fp += x[s] * cv;
+            f += x[s] * (RM * T * (hRT - 1.0) - ef);
+            fp += x[s] * (RM * (cpR - 1.0));
         }
         f = Grp<G>::sum(f) - e;
         fp = Grp<G>::sum(fp);
@@ -116,7 +168,7 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
                     hi = T;
                 else
                     lo = T;
-                double Tn = T - f / fp;
+                double Tn = T - f * frcp(fp);
                 if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
                 const double dT = Tn - T;
                 T = Tn;
@@ -132,55 +184,64 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
 
 template <typename JT>
 struct SlotMem {
-    double *x, *x0, *c, *hRT, *gRT, *es, *wd, *Q, *dQdT, *qtb;
-    JT *dTdr, *w, *u, *D, *A;
-    __device__ __forceinline__ void carve(char *base, int ns, int nr, int nD) {
-        const int n = ns + 1;
+    double *x, *x0, *c, *hRT, *gRT, *es, *wd, *Q, *part;
+    JT *D, *dTdr, *w, *u, *A, *dQdT, *qtb, *A1, *A2;
+    JT *cJ, *hJ;   // concentrations and h/RT in the Jacobian type (FP32 path)
+    __device__ __forceinline__ void carve(char *base, const DeviceMech &m) {
+        const int ns = m.ns, n = ns + 1, nr = m.nr;
+        constexpr int jt = (int)sizeof(JT);
         double *p = reinterpret_cast<double *>(base);
         x = p;
         x0 = x + n;
         c = x0 + n;
-        hRT = c + ns;
-        gRT = hRT + ns;
-        es = gRT + ns;
+        hRT = c + ns + 1;
+        gRT = hRT + ns + 1;
+        es = gRT + ns + 1;
         wd = es + ns;
-        Q = wd + ns;
-        dQdT = Q + nr;
-        qtb = dQdT + nr;
-        JT *q = reinterpret_cast<JT *>(qtb + nr);
-        dTdr = q;
+        char *q = base + ((2LL * n + 3LL * (ns + 1) + 2LL * ns) * 8 + 15) / 16 * 16;
+        dTdr = reinterpret_cast<JT *>(q);
         w = dTdr + ns;
         u = w + ns;
-        D = u + ns;
-        A = D + nD;
+        if (jt == 4) {
+            cJ = u + ns;
+            hJ = cJ + ns + 1;
+        } else {
+            cJ = reinterpret_cast<JT *>(c);
+            hJ = reinterpret_cast<JT *>(hRT);
+        }
+        q += slot_small_bytes(ns, jt);
+        part = reinterpret_cast<double *>(q);
+        D = reinterpret_cast<JT *>(q);
+        q += ((long long)dreg8_for(m.nD, m.n_items, jt) * 8 + 15) / 16 * 16;
+        // union: per-reaction rates, then (after the D entries) the matrix
+        Q = reinterpret_cast<double *>(q);
+        dQdT = reinterpret_cast<JT *>(Q + nr);
+        qtb = dQdT + nr;
+        A1 = qtb + nr;
+        A2 = A1 + nr;
+        A = reinterpret_cast<JT *>(q);
     }
 };
 
-// Bytes of one slot for the kernel's carve (must match slot_smem_bytes).
-__host__ __device__ inline long long slot_bytes(int ns, int nr, int nD, int jt) {
-    const int n = ns + 1;
-    long long dbl = 2LL * n + 5LL * ns + 3LL * nr;
-    long long jtn = 3LL * ns + nD + (long long)n * (n + 1);
-    return ((dbl * 8 + jtn * jt) + 15) / 16 * 16;
-}
-
-// Sources, Jacobian and one Newton update for every slot of the warp.
-// Inputs per slot: x, x0, T, h.  Outputs: x <- x + delta, the scaled norm,
-// and flags for a singular pivot or a non-finite update.
+// Sources, Jacobian and one Newton update of Eq. 29 for every slot of the
+// warp.  Inputs per slot: x, x0, T, h.  Outputs: x <- x + delta, the scaled
+// norm, and a flag for a singular pivot or a non-finite update.
 template <int G, typename JT>
-__device__ void newton_iteration(const DeviceMech &m, SlotMem<JT> &sm, int sl, double T, double h,
-                                 double atol_rho, double atol_e, double rtol, double &norm,
-                                 bool &bad) {
+__device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem<JT> &sm, int sl,
+                                 double T, double h, double atol_rho, double atol_e, double rtol,
+                                 double escale, double &norm, bool &bad, double &T_pred) {
     const int ns = m.ns, nr = m.nr, n = ns + 1, lda = n + 1;
-    const double invT = 1.0 / T;
+    constexpr bool f32 = sizeof(JT) == 4;
+    const double invT = frcp(T);
     const double lnT = log(T);
     const double lnPaRT = log(kPa / kR) - lnT;
 
-    // concentrations and thermo (species lane-strided)
+    // 1. concentrations and thermodynamics (species)
     double ctot = 0.0, rhocv = 0.0;
     for (int s = sl; s < ns; s += G) {
         const double *spr = m.sp + s * kSpStride;
-        const double ci = sm.x[s] * __ldg(spr + 1);
+        const double xs = sm.x[s];
+        const double ci = xs * __ldg(spr + 1);
         sm.c[s] = ci;
         ctot += ci;
         const double *th = thermo_row(m, s, T);
@@ -190,161 +251,209 @@ __device__ void newton_iteration(const DeviceMech &m, SlotMem<JT> &sm, int sl, d
         const double RM = __ldg(spr + 2);
         sm.hRT[s] = hRT;
         sm.gRT[s] = hRT - sR;
-        const double es = RM * T * (hRT - 1.0) - __ldg(spr + 3);
-        sm.es[s] = es;
-        rhocv += sm.x[s] * RM * (cpR - 1.0);
+        sm.es[s] = RM * T * (hRT - 1.0) - __ldg(spr + 3);
+        rhocv += xs * (RM * (cpR - 1.0));
+        if (f32) {
+            sm.cJ[s] = (JT)ci;
+            sm.hJ[s] = (JT)hRT;
+        }
+    }
+    if (f32 && sl == 0) {
+        sm.cJ[ns] = (JT)1;
+        sm.hJ[ns] = (JT)0;
     }
     ctot = Grp<G>::sum(ctot);
     rhocv = Grp<G>::sum(rhocv);
-    const double dTde = 1.0 / rhocv;
+    const double dTde = frcp(rhocv);
     for (int s = sl; s < ns; s += G) sm.dTdr[s] = (JT)(-sm.es[s] * dTde);
     __syncwarp();
 
-    // rates, progress rates and rate derivatives (reactions lane-strided):
-    // Eq. 23 forward rate, Eq. 24 equilibrium constant, Eq. 25 progress rate
+    // 2. rates per reaction: Eq. 23 forward rate, Eq. 24 equilibrium
+    //    constant, Eq. 25 progress rate, and their temperature derivatives
     for (int r = sl; r < nr; r += G) {
         const double *rd = m.rxn_d + (size_t)r * kRxnDStride;
-        const int *ri = m.rxn_i + (size_t)r * kRxnIStride;
-        const double lnA = __ldg(rd + 0), beta = __ldg(rd + 1), EaR = __ldg(rd + 2),
-                     dnu = __ldg(rd + 3);
-        const int rs0 = __ldg(ri + 0), rs1 = __ldg(ri + 1), rs2 = __ldg(ri + 2);
-        const int ps0 = __ldg(ri + 3), ps1 = __ldg(ri + 4), ps2 = __ldg(ri + 5);
-        const int nup = __ldg(ri + 6), flags = __ldg(ri + 7);
-        const int nr0 = nup & 3, nr1 = (nup >> 2) & 3, nr2 = (nup >> 4) & 3;
-        const int np0 = (nup >> 8) & 3, np1 = (nup >> 10) & 3, np2 = (nup >> 12) & 3;
+        const double lnA = __ldg(rd + 0), beta = __ldg(rd + 1), EaR = __ldg(rd + 2), dnu = __ldg(rd + 3);
+        const int fr = __ldg(m.rxn_f + 2 * r), fpw = __ldg(m.rxn_f + 2 * r + 1);
+        const int a0 = fr & 0xff, a1 = (fr >> 8) & 0xff, a2 = (fr >> 16) & 0xff;
+        const int b0 = fpw & 0xff, b1 = (fpw >> 8) & 0xff, b2 = (fpw >> 16) & 0xff;
+        const double Pf = sm.c[a0] * sm.c[a1] * sm.c[a2];
+        const double Pb = sm.c[b0] * sm.c[b1] * sm.c[b2];
+        const double sg = (sm.gRT[b0] + sm.gRT[b1] + sm.gRT[b2]) - (sm.gRT[a0] + sm.gRT[a1] + sm.gRT[a2]);
         const double lnkf = lnA + beta * lnT - EaR * invT;
-        double sg = 0.0, sh = 0.0;
-        double pr0 = 1.0, pr1 = 1.0, pr2 = 1.0, pp0 = 1.0, pp1 = 1.0, pp2 = 1.0;
-        if (rs0 >= 0) { pr0 = ipow3(sm.c[rs0], nr0); sg -= nr0 * sm.gRT[rs0]; sh -= nr0 * sm.hRT[rs0]; }
-        if (rs1 >= 0) { pr1 = ipow3(sm.c[rs1], nr1); sg -= nr1 * sm.gRT[rs1]; sh -= nr1 * sm.hRT[rs1]; }
-        if (rs2 >= 0) { pr2 = ipow3(sm.c[rs2], nr2); sg -= nr2 * sm.gRT[rs2]; sh -= nr2 * sm.hRT[rs2]; }
-        if (ps0 >= 0) { pp0 = ipow3(sm.c[ps0], np0); sg += np0 * sm.gRT[ps0]; sh += np0 * sm.hRT[ps0]; }
-        if (ps1 >= 0) { pp1 = ipow3(sm.c[ps1], np1); sg += np1 * sm.gRT[ps1]; sh += np1 * sm.hRT[ps1]; }
-        if (ps2 >= 0) { pp2 = ipow3(sm.c[ps2], np2); sg += np2 * sm.gRT[ps2]; sh += np2 * sm.hRT[ps2]; }
         const double lnKc = dnu * lnPaRT - sg;
-        const double kf = exp(lnkf);
-        const double kb = exp(lnkf - lnKc);
-        const double Pf = pr0 * pr1 * pr2, Pb = pp0 * pp1 * pp2;
-        const int tb = flags & 1;
-        const int doff = (flags >> 1) & 0xFFFFF, dcnt = (flags >> 21) & 0x3FF;
+        const double kf = fexp(lnkf, tab);
+        const double kb = fexp(lnkf - lnKc, tab);
         double CM = 1.0;
+        const bool tb = (fr >> 24) & 1;
         if (tb) {
             CM = ctot;
-            for (int j = doff; j < doff + dcnt; ++j)
-                CM += __ldg(m.deff + j) * sm.c[__ldg(m.dcol + j) & 0xff];
+            const int e0 = __ldg(m.eff_ptr + r), e1 = __ldg(m.eff_ptr + r + 1);
+            for (int e = e0; e < e1; ++e) CM += __ldg(m.eff_c + e) * sm.c[__ldg(m.eff_sp + e)];
         }
         const double fwd = kf * Pf, rev = kb * Pb, q = fwd - rev;
         sm.Q[r] = CM * q;
-        sm.qtb[r] = tb ? q : 0.0;
-        const double dlnkf = beta * invT + EaR * invT * invT;
-        const double dlnKc = (sh - dnu) * invT;
-        sm.dQdT[r] = CM * (fwd * dlnkf - rev * (dlnkf - dlnKc));
-        // d Q_r / d rho_k for the species the rate depends on, without the
-        // all-ones third-body part (added below as a rank-1 term)
-        for (int j = doff; j < doff + dcnt; ++j) {
-            const int pk = __ldg(m.dcol + j);
-            const int k = pk & 0xff, rsl = (pk >> 8) & 3, psl = (pk >> 10) & 3;
-            double dPf = 0.0, dPb = 0.0;
-            if (rsl == 0) dPf = nr0 * ipow3(sm.c[k], nr0 - 1) * pr1 * pr2;
-            else if (rsl == 1) dPf = nr1 * ipow3(sm.c[k], nr1 - 1) * pr0 * pr2;
-            else if (rsl == 2) dPf = nr2 * ipow3(sm.c[k], nr2 - 1) * pr0 * pr1;
-            if (psl == 0) dPb = np0 * ipow3(sm.c[k], np0 - 1) * pp1 * pp2;
-            else if (psl == 1) dPb = np1 * ipow3(sm.c[k], np1 - 1) * pp0 * pp2;
-            else if (psl == 2) dPb = np2 * ipow3(sm.c[k], np2 - 1) * pp0 * pp1;
-            const double d = CM * (kf * dPf - kb * dPb) + __ldg(m.deff + j) * q;
-            sm.D[j] = (JT)(d * __ldg(m.sp + k * kSpStride + 1));
+        if (f32) {
+            // Jacobian-only quantities in FP32 from FP32 copies
+            const float* rf = m.rxn_df + (size_t)r * kRxnDStride;
+            const JT A1v = (JT)(CM * kf), A2v = (JT)(CM * kb);
+            sm.A1[r] = A1v;
+            sm.A2[r] = A2v;
+            sm.qtb[r] = tb ? (JT)q : (JT)0;
+            const JT shf = (sm.hJ[b0] + sm.hJ[b1] + sm.hJ[b2]) - (sm.hJ[a0] + sm.hJ[a1] + sm.hJ[a2]);
+            const JT iT = (JT)invT;
+            const JT dlnkf = (JT)__ldg(rf + 1) * iT * iT + (JT)__ldg(rf) * iT;
+            const JT dlnKc = (shf - (JT)__ldg(rf + 2)) * iT;
+            sm.dQdT[r] = A1v * (JT)Pf * dlnkf - A2v * (JT)Pb * (dlnkf - dlnKc);
+        } else {
+            const double sh = (sm.hRT[b0] + sm.hRT[b1] + sm.hRT[b2]) - (sm.hRT[a0] + sm.hRT[a1] + sm.hRT[a2]);
+            sm.qtb[r] = tb ? (JT)q : (JT)0;
+            sm.A1[r] = (JT)(CM * kf);
+            sm.A2[r] = (JT)(CM * kb);
+            const double dlnkf = fma(EaR * invT, invT, beta * invT);
+            const double dlnKc = (sh - dnu) * invT;
+            sm.dQdT[r] = (JT)(CM * (fwd * dlnkf - rev * (dlnkf - dlnKc)));
         }
     }
     __syncwarp();
 
-    // species sources (Eq. 26) and the two rank-1 vectors of the Jacobian
-    double wde = 0.0, wE = 0.0, uE = 0.0;
+    // 3. species sources (Eq. 26) and the rank-1 vectors of the Jacobian, as
+    //    fixed-size chunks of each species' reaction list, then per species
+    for (int it = sl; it < m.n_items; it += G) {
+        const int e0 = __ldg(m.it_ptr + it), e1 = __ldg(m.it_ptr + it + 1);
+        double sq = 0.0;
+        JT sdq = 0, squ = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int r = __ldg(m.sp_r + e);
+            const double nu = __ldg(m.sp_nu + e);
+            const JT nuj = f32 ? (JT)__ldg(m.sp_nuf + e) : (JT)nu;
+            sq = fma(nu, sm.Q[r], sq);
+            sdq += nuj * sm.dQdT[r];
+            squ += nuj * sm.qtb[r];
+        }
+        sm.part[3 * it] = sq;
+        sm.part[3 * it + 1] = (double)sdq;
+        sm.part[3 * it + 2] = (double)squ;
+    }
+    __syncwarp();
+    double wde = 0.0;
     for (int s = sl; s < ns; s += G) {
         double sq = 0.0, sdq = 0.0, squ = 0.0;
-        const int e0 = __ldg(m.sp_ptr + s), e1 = __ldg(m.sp_ptr + s + 1);
-        for (int e = e0; e < e1; ++e) {
-            const int ent = __ldg(m.sp_ent + e);
-            const int r = ent >> 8;
-            const double nu = (double)(signed char)(ent & 0xff);
-            sq += nu * sm.Q[r];
-            sdq += nu * sm.dQdT[r];
-            squ += nu * sm.qtb[r];
+        const int i0 = __ldg(m.sp_item_ptr + s), i1 = __ldg(m.sp_item_ptr + s + 1);
+        for (int it = i0; it < i1; ++it) {
+            sq += sm.part[3 * it];
+            sdq += sm.part[3 * it + 1];
+            squ += sm.part[3 * it + 2];
         }
         const double M = __ldg(m.sp + s * kSpStride);
-        const double ef = __ldg(m.sp + s * kSpStride + 3);
-        const double wds = M * sq, ws = M * sdq, us = M * squ;
+        const double wds = M * sq;
         sm.wd[s] = wds;
-        sm.w[s] = (JT)ws;
-        sm.u[s] = (JT)us;
-        wde -= ef * wds;
-        wE += ef * ws;
-        uE += ef * us;
+        sm.w[s] = (JT)(M * sdq);
+        sm.u[s] = (JT)(M * squ);
+        wde -= __ldg(m.sp + s * kSpStride + 3) * wds;
     }
     wde = Grp<G>::sum(wde);
-    wE = Grp<G>::sum(wE);
-    uE = Grp<G>::sum(uE);
     __syncwarp();
 
-    // right-hand side -F = -(x - x0 - h Omega(x))
+    // 4. D entries: d Q_r / d rho_k without the all-ones third-body part,
+    //    grouped so that each group is one uniform loop body
+    for (int j = sl; j < m.nD; j += G) {
+        const int i0 = __ldg(m.d_i0 + j), i1 = __ldg(m.d_i1 + j);
+        const int r = i0 & 0xffff;
+        const int fa = i1 & 0xff, fb = (i1 >> 8) & 0xff, ba = (i1 >> 16) & 0xff, bb = (i1 >> 24) & 0xff;
+        JT d;
+        if (f32) {
+            const float *dc = m.d_cf + 3 * (size_t)j;
+            if (j < m.nD_F) {
+                d = (JT)__ldg(dc) * sm.A1[r] * (sm.cJ[fa] * sm.cJ[fb]);
+            } else if (j < m.nD_B) {
+                d = -(JT)__ldg(dc + 1) * sm.A2[r] * (sm.cJ[ba] * sm.cJ[bb]);
+            } else if (j < m.nD_FB) {
+                d = (JT)__ldg(dc) * sm.A1[r] * (sm.cJ[fa] * sm.cJ[fb]) -
+                    (JT)__ldg(dc + 1) * sm.A2[r] * (sm.cJ[ba] * sm.cJ[bb]);
+            } else {
+                d = 0;
+            }
+            d += (JT)__ldg(dc + 2) * sm.qtb[r];
+        } else {
+            const double *dc = m.d_c + 3 * (size_t)j;
+            double dd;
+            if (j < m.nD_F) {
+                dd = __ldg(dc) * sm.A1[r] * (sm.c[fa] * sm.c[fb]);
+            } else if (j < m.nD_B) {
+                dd = -__ldg(dc + 1) * sm.A2[r] * (sm.c[ba] * sm.c[bb]);
+            } else if (j < m.nD_FB) {
+                dd = __ldg(dc) * sm.A1[r] * (sm.c[fa] * sm.c[fb]) -
+                     __ldg(dc + 1) * sm.A2[r] * (sm.c[ba] * sm.c[bb]);
+            } else {
+                dd = 0.0;
+            }
+            d = (JT)fma(__ldg(dc + 2), (double)sm.qtb[r], dd);
+        }
+        sm.D[j] = d;
+    }
+    __syncwarp();
+    // the per-reaction arrays are dead from here on; the matrix takes their place
+
+    // 5. right-hand side -F = -(x - x0 - h Omega(x))
     for (int i = sl; i < n; i += G) {
         const double om = i < ns ? sm.wd[i] : wde;
         sm.A[i * lda + n] = (JT)(-(sm.x[i] - sm.x0[i] - h * om));
     }
-    // species rows of A = I - h J
-    const JT hj = (JT)h;
-    for (int idx = sl; idx < ns * n; idx += G) {
-        const int s = idx / n, k = idx - (idx / n) * n;
-        JT J;
-        if (k < ns) {
-            J = sm.w[s] * sm.dTdr[k] + sm.u[s] * (JT)__ldg(m.sp + k * kSpStride + 1);
-            const int g = __ldg(m.jmap + s * ns + k);
-            if (g >= 0) {
-                JT acc = 0;
-                const int e0 = __ldg(m.j_ptr + g), e1 = __ldg(m.j_ptr + g + 1);
-                for (int e = e0; e < e1; ++e) {
-                    const int ent = __ldg(m.j_ent + e);
-                    acc += (JT)(signed char)(ent & 0xff) * sm.D[ent >> 8];
-                }
-                J += (JT)__ldg(m.sp + s * kSpStride) * acc;
-            }
+
+    // 6. species rows of -h J (longest gather lists first, so the lanes of a
+    //    pass run lists of nearly equal length)
+    const JT mh = (JT)(-h);
+    for (int p = sl; p < m.nJ; p += G) {
+        const int sk = __ldg(m.j_sk + p);
+        const int s = sk >> 8, k = sk & 0xff;
+        JT J = sm.w[s] * sm.dTdr[k] + sm.u[s] * (JT)__ldg(m.sp + k * kSpStride + 1);
+        const int e0 = __ldg(m.j_ptr + p), e1 = __ldg(m.j_ptr + p + 1);
+        if (f32) {
+            for (int e = e0; e < e1; ++e) J += (JT)__ldg(m.j_cf + e) * sm.D[__ldg(m.j_d + e)];
         } else {
-            J = sm.w[s] * (JT)dTde;
+            for (int e = e0; e < e1; ++e) J += (JT)__ldg(m.j_c + e) * sm.D[__ldg(m.j_d + e)];
         }
-        sm.A[s * lda + k] = (s == k ? (JT)1 : (JT)0) - hj * J;
+        sm.A[s * lda + k] = mh * J;
     }
-    // energy row: J_ek = -sum_s e_f,s J_sk, gathered per column
+    for (int s = sl; s < ns; s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * (JT)dTde);
+    __syncwarp();
+    // energy row: -h J_ek = -sum_s e_f,s (-h J_sk) (dense column sums)
     for (int k = sl; k < n; k += G) {
-        JT J;
-        if (k < ns) {
-            JT acc = 0;
-            const int e0 = __ldg(m.col_ptr + k), e1 = __ldg(m.col_ptr + k + 1);
-            for (int e = e0; e < e1; ++e) {
-                const int j = __ldg(m.col_ent + e);
-                acc += (JT)__ldg(m.dEf + j) * sm.D[j];
-            }
-            J = -((JT)wE * sm.dTdr[k] + (JT)uE * (JT)__ldg(m.sp + k * kSpStride + 1) + acc);
-        } else {
-            J = -(JT)(wE * dTde);
+        JT acc = 0;
+        for (int s = 0; s < ns; ++s) acc += (JT)__ldg(m.sp + s * kSpStride + 3) * sm.A[s * lda + k];
+        sm.A[ns * lda + k] = -acc;
+    }
+    __syncwarp();
+    for (int i = sl; i < n; i += G) sm.A[i * lda + i] += (JT)1;
+    if (f32) {
+        // solve for (delta rho, delta e / S), S = E_scale / rho: the energy
+        // row and column then sit on the species' scale, which keeps the
+        // FP32 elimination well conditioned
+        const JT S = (JT)escale, iS = (JT)(1.0 / escale);
+        for (int k = sl; k < ns; k += G) {
+            sm.A[ns * lda + k] *= iS;
+            sm.A[k * lda + ns] *= S;
         }
-        sm.A[ns * lda + k] = (k == ns ? (JT)1 : (JT)0) - hj * J;
+        if (sl == 0) sm.A[ns * lda + n] *= iS;
     }
     __syncwarp();
 
-    // Gaussian elimination with row partial pivoting on [A | -F] (Sec. 3.2),
-    // ties to the lowest row; the pivot's reciprocal replaces the diagonal
+    // 7. Gaussian elimination with row partial pivoting on [A | -F]
+    //    (Sec. 3.2), ties to the lowest row; the pivot's reciprocal replaces
+    //    the diagonal
     bool sing = false;
     for (int j = 0; j < n; ++j) {
-        double best = -1.0;
+        unsigned long long best = 0;
         int bi = n;
         for (int i = j + sl; i < n; i += G) {
-            const double v = fabs((double)sm.A[i * lda + j]);
-            if (v > best) {
-                best = v;
+            const unsigned long long kk = abs_key(sm.A[i * lda + j]);
+            if (bi == n || kk > best) {
+                best = kk;
                 bi = i;
             }
         }
         Grp<G>::argmax(best, bi);
-        if (!(best > 0.0) || isinf(best)) sing = true;
+        if (best == 0 || key_is_inf(best, JT(0))) sing = true;
         if (bi != j && bi < n) {
             for (int k = j + sl; k <= n; k += G) {
                 const JT t = sm.A[j * lda + k];
@@ -353,15 +462,23 @@ __device__ void newton_iteration(const DeviceMech &m, SlotMem<JT> &sm, int sl, d
             }
         }
         __syncwarp();
-        const JT inv = (JT)1 / sm.A[j * lda + j];
+        const JT inv = frcp(sm.A[j * lda + j]);
         for (int i = j + 1 + sl; i < n; i += G) sm.A[i * lda + j] *= inv;
         __syncwarp();
         if (sl == 0) sm.A[j * lda + j] = inv;
         const int cols = n - j;
         const int tot = (n - j - 1) * cols;
-        for (int e = sl; e < tot; e += G) {
-            const int i = j + 1 + e / cols, k = j + 1 + e % cols;
+        int e = sl;
+        int i = j + 1 + e / cols, k = j + 1 + e % cols;
+        const int di = G / cols, dk = G % cols;
+        for (; e < tot; e += G) {
             sm.A[i * lda + k] -= sm.A[i * lda + j] * sm.A[j * lda + k];
+            i += di;
+            k += dk;
+            if (k > n) {
+                k -= cols;
+                ++i;
+            }
         }
         __syncwarp();
     }
@@ -373,22 +490,32 @@ __device__ void newton_iteration(const DeviceMech &m, SlotMem<JT> &sm, int sl, d
         for (int i = sl; i < j; i += G) sm.A[i * lda + n] -= sm.A[i * lda + j] * dj;
         __syncwarp();
     }
-    // update and convergence norm
-    double nrm = 0.0;
+
+    // 8. update, convergence norm, and the linearised temperature of the
+    //    new iterate (dT = (de - sum_s e_s^sens drho_s) / (rho cv)) as the
+    //    next recovery's starting guess
+    double nrm = 0.0, des = 0.0;
     int nonfinite = 0;
     for (int i = sl; i < n; i += G) {
-        const double d = (double)sm.A[i * lda + n];
+        double d = (double)sm.A[i * lda + n];
+        if (f32 && i == ns) d *= escale;
+        des += i < ns ? -sm.es[i] * d : d;
         const double xi = sm.x[i] + d;
         sm.x[i] = xi;
         if (!isfinite(xi)) nonfinite = 1;
         const double at = i < ns ? atol_rho : atol_e;
-        nrm = fmax(nrm, fabs(d) / (rtol * fabs(xi) + at));
+        const double den = fma(rtol, fabs(xi), at);
+        // a zero scale counts a nonzero update as infinitely large
+        const double ri = den > 0.0 ? fabs(d) * frcp(den) : (d != 0.0 ? CUDART_INF : 0.0);
+        nrm = fmax(nrm, ri);
     }
     nrm = Grp<G>::max(nrm);
     nonfinite = Grp<G>::any(nonfinite);
+    des = Grp<G>::sum(des);
     __syncwarp();
     norm = nrm;
     bad = sing || nonfinite;
+    T_pred = T + des * dTde;
 }
 
 template <int G, typename JT>
@@ -400,14 +527,23 @@ __global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, St
     const int slot = lane / G;
     const int sl = lane - slot * G;
     const int ns = m.ns, n = ns + 1;
-    const long long sbytes = slot_bytes(ns, m.nr, m.nD, (int)sizeof(JT));
+    double *tab = reinterpret_cast<double *>(smem);
+    for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) tab[i] = m.exp_tab[i];
+    const long long sbytes = slot_bytes_for(ns, m.nr, m.nD, m.n_items, (int)sizeof(JT));
     SlotMem<JT> sm;
-    sm.carve(smem + (size_t)(warp * S + slot) * sbytes, ns, m.nr, m.nD);
+    sm.carve(smem + kBlockHeaderBytes + (size_t)(warp * S + slot) * sbytes, m);
+    // sentinel species: concentration 1, no Gibbs or enthalpy contribution
+    if (sl == 0) {
+        sm.c[ns] = 1.0;
+        sm.hRT[ns] = 0.0;
+        sm.gRT[ns] = 0.0;
+    }
+    __syncthreads();
 
     int state = kFree;
     long long cell = -1;
     double T = 1500.0, T0 = 1500.0, Tin = CUDART_NAN, h = 0.0, norm_prev = CUDART_INF;
-    double atol_rho = 0.0, atol_e = 0.0;
+    double atol_rho = 0.0, atol_e = 0.0, escale = 1.0;
     int k = 0, level = 0, attempts = 0, iters = 0, subs = 0, fails = 0;
     long long t_units = 0;
     const long long total = 1LL << o.max_halvings;
@@ -478,6 +614,7 @@ __global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, St
             if (loading) {
                 atol_rho = o.atol_rel * rt;
                 atol_e = o.atol_rel * es;
+                escale = es > 0.0 && rt > 0.0 ? es / rt : 1.0;
                 T = b.T_in ? b.T_in[cell] : 1500.0;
                 if (nonfin || !(rt > 0.0))
                     write_fail(kCellBadInput);
@@ -490,11 +627,11 @@ __global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, St
             double Tr = T;
             bool ok = false;
             recover_T<G>(m, sm.x, sl, needT, T, Tr, ok);
-            __syncwarp();
             int neg = 0;
             for (int i = sl; i < ns; i += G)
                 if (sm.x[i] < -atol_rho) neg = 1;
             neg = Grp<G>::any(neg);
+            __syncwarp();
             if (state == kInitT) {
                 if (!ok) {
                     write_fail(kCellTFailed);
@@ -561,10 +698,12 @@ __global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, St
             continue;
         }
         // one Newton iteration of Eq. 29 for every slot
-        double norm = 0.0;
+        double norm = 0.0, T_pred = T;
         bool bad = false;
-        newton_iteration<G, JT>(m, sm, sl, T, h, atol_rho, atol_e, o.rtol, norm, bad);
+        newton_iteration<G, JT>(m, tab, sm, sl, T, h, atol_rho, atol_e, o.rtol, escale, norm, bad, T_pred);
         if (state == kNewtonReady) {
+            // start the next temperature recovery from the linear prediction
+            if (T_pred > kTlo && T_pred < kThi) T = T_pred;
             ++iters;
             if (bad) {
                 substep_fail();
