@@ -103,7 +103,7 @@ typedef struct chem_options {
 /* Fills *o with the defaults: FP64, rtol 1e-10, atol_rel 1e-12,
  * max_newton 12, max_halvings 20, max_attempts 1000, point_implicit 0,
  * div_check 1, lanes_per_cell 0, autotune 0, hbm_budget_bytes 0,
- * max_newton_mixed 30. */
+ * max_newton_mixed 12. */
 int chem_default_options(chem_options *o);
 
 /* Validates the mechanism (index ranges, 1..3 species per side with

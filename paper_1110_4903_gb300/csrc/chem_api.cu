@@ -564,7 +564,7 @@ int chem_default_options(chem_options *o) {
     o->lanes_per_cell = 0;
     o->autotune = 0;
     o->hbm_budget_bytes = 0;
-    o->max_newton_mixed = 30;
+    o->max_newton_mixed = 12;
     return CHEM_OK;
 }
 
