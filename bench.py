@@ -194,14 +194,19 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_path(torch, ch, rho0, e0, T_in, dt, precision, steps, warmup, flush, stream, want_stats):
+def time_path(torch, ch, rho0, e0, T_in, dt, precision, steps, warmup, flush, stream, want_stats,
+              graph=False):
     """Times `steps` advances (after `warmup`) on `stream`; returns per-step
-    kernel-only and whole-step times (ms) and per-cell counters."""
+    kernel-only and whole-step times (ms) and per-cell counters.  With
+    graph=True each step is a launch of a captured graph of the step."""
     n = e0.shape[0]
     rho = torch.empty_like(rho0)
     e = torch.empty_like(e0)
     st = torch.empty(n, dtype=torch.int32, device=e0.device)
     it = torch.empty(n, dtype=torch.int32, device=e0.device)
+    g = None
+    if graph:
+        g = ch.graph(rho, e, dt, T_in=T_in, status=st, newton_iters=it, precision=precision)
     step_ms, kern_ms = [], []
     with torch.cuda.stream(stream):
         for i in range(warmup + steps):
@@ -213,12 +218,17 @@ def time_path(torch, ch, rho0, e0, T_in, dt, precision, steps, warmup, flush, st
             rho.copy_(rho0)
             e.copy_(e0)
             k0.record(stream)
-            ch.advance(rho, e, dt, T_in=T_in, status=st, newton_iters=it, precision=precision,
-                       stream=stream)
+            if g is not None:
+                g.launch(stream)
+            else:
+                ch.advance(rho, e, dt, T_in=T_in, status=st, newton_iters=it, precision=precision,
+                           stream=stream)
             b.record(stream)
             if i >= warmup:
                 step_ms.append((a, k0, b))
         stream.synchronize()
+    if g is not None:
+        g.close()
     tot = [a.elapsed_time(b) for a, k0, b in step_ms]
     ker = [k0.elapsed_time(b) for a, k0, b in step_ms]
     stats = None
@@ -243,6 +253,8 @@ def main():
                     help="both: time FP64 and mixed, headline = mixed")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per cell (0: the library's choice)")
     ap.add_argument("--workload", default=WORKLOAD, help="named workload of synth.workload")
+    ap.add_argument("--graph", action="store_true", help="time captured-graph steps")
+    ap.add_argument("--autotune", action="store_true", help="autotune the launch shape first")
     ap.add_argument("--cells", type=int, default=0,
                     help="time the first CELLS cells only (a smaller case for profiling)")
     args = ap.parse_args()
@@ -287,6 +299,8 @@ def main():
     wall = 0.0
     for name, ch in handles.items():
         prec = chem.MIXED if name == "mixed" else chem.FP64
+        if args.autotune:
+            ch.autotune(rho0, e0, dt, T_in=T, precision=prec, stream=stream)
         # untimed statistics launch: Newton iterations for the work model
         _, _, stats = time_path(torch, ch, rho0, e0, T, dt, prec, 1, 0, flush, stream, True)
         launches0 = ch.launch_count()
@@ -296,7 +310,7 @@ def main():
         with Clocks(local) as ck:
             t0 = time.perf_counter()
             tot, ker, _ = time_path(torch, ch, rho0, e0, T, dt, prec, args.steps, args.warmup, flush,
-                                    stream, False)
+                                    stream, False, graph=args.graph)
             torch.cuda.synchronize()
             w = time.perf_counter() - t0
         launches = (ch.launch_count() - launches0) * args.steps // (args.steps + args.warmup)
@@ -373,7 +387,8 @@ def main():
                            "lanes_per_cell": hr["lanes_per_cell"],
                            "l2": "flushed (256 MiB write) before every step; state restored from "
                                  "a device copy inside the step",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "graph": bool(args.graph), "autotuned": bool(args.autotune)},
                 "kernel_ms_per_step": hr["kernel_ms_per_step"], "wall_s": wall,
                 "newton_iters_mean": hr["newton_iters_mean"],
                 "newton_iters_max": hr["newton_iters_max"], "cells_ok": hr["cells_ok"],

@@ -182,6 +182,28 @@ int chem_state_from_tpy(chem_handle_t h, int64_t n_cells, int64_t ld, const doub
 int chem_temperature(chem_handle_t h, int64_t n_cells, int64_t ld, const double *rho_s,
                      const double *e, const double *T_guess, double *T_out, void *stream);
 
+/* Autotuner: times every launch shape the shared memory allows -- lanes per
+ * cell (cells per warp = 32/lanes) and warps per block -- on a strided
+ * sample of at most 16,384 of the given cells (device buffers, same layout
+ * as chem_advance_ex; the cells themselves are not modified: the sample is
+ * copied), keeps the fastest for `precision` on this handle and returns it.
+ * Synchronous.  With chem_options.autotune = 1 the first chem_advance_ex of
+ * each precision runs it on its own cells first. */
+int chem_autotune(chem_handle_t h, int32_t precision, int64_t n_cells, int64_t ld,
+                  const double *rho_s, const double *e, double dt, const double *T_in,
+                  void *stream, int32_t *lanes_out, int32_t *wpb_out);
+
+/* A captured CUDA graph of one chemistry step (work-counter reset + the
+ * persistent step kernel) with fixed arguments, for time loops that step the
+ * same device buffers again and again: the work stealing happens inside the
+ * kernel, the graph removes the per-step launch work on the host.  The graph
+ * owns its work counter.  chem_graph_launch is asynchronous on `stream`;
+ * launches of one graph must not overlap on the device. */
+typedef struct chem_graph_s *chem_graph_t;
+int chem_graph_create(chem_handle_t h, const chem_advance_args *a, chem_graph_t *out);
+int chem_graph_launch(chem_graph_t g, void *stream);
+int chem_graph_destroy(chem_graph_t g);
+
 /* Lanes per cell the handle uses for `precision` (after autotuning, if on). */
 int chem_get_lanes_per_cell(chem_handle_t h, int32_t precision, int32_t *lanes);
 

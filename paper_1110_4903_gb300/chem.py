@@ -75,6 +75,10 @@ def lib():
             "chem_temperature": [p, i64, i64, p, p, p, p, p],
             "chem_get_lanes_per_cell": [p, i32, p],
             "chem_launch_count": [p, p],
+            "chem_autotune": [p, i32, i64, i64, p, p, d, p, p, p, p],
+            "chem_graph_create": [p, p, p],
+            "chem_graph_launch": [p, p],
+            "chem_graph_destroy": [p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -114,6 +118,27 @@ def _stream_ptr(stream):
         import torch
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream)
+
+
+class StepGraph:
+    """A captured chemistry step (chem_graph_*)."""
+
+    def __init__(self, g):
+        self.g = g
+
+    def launch(self, stream=None):
+        check(lib().chem_graph_launch(self.g, _stream_ptr(stream)))
+
+    def close(self):
+        if self.g:
+            check(lib().chem_graph_destroy(self.g))
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Chem:
@@ -187,6 +212,27 @@ class Chem:
         n = int(e.shape[0])
         check(lib().chem_temperature(self.h, n, int(rho.stride(0)), _ptr(rho), _ptr(e),
                                      _ptr(T_guess), _ptr(T_out), _stream_ptr(stream)))
+
+    def autotune(self, rho, e, dt, *, n_cells=None, T_in=None, precision=FP64, stream=None):
+        """Times the launch shapes on a sample of these cells (not modified)
+        and keeps the fastest; returns (lanes_per_cell, warps_per_block)."""
+        n = int(e.shape[0]) if n_cells is None else int(n_cells)
+        lanes, wpb = C.c_int32(), C.c_int32()
+        check(lib().chem_autotune(self.h, int(precision), n, int(rho.stride(0)), rho.data_ptr(),
+                                  e.data_ptr(), float(dt), _ptr(T_in), _stream_ptr(stream),
+                                  C.byref(lanes), C.byref(wpb)))
+        return lanes.value, wpb.value
+
+    def graph(self, rho, e, dt, *, n_cells=None, T_in=None, T_out=None, status=None,
+              newton_iters=None, substeps=None, failures=None, precision=-1, lanes=0):
+        """Captures one step of these buffers as a CUDA graph (StepGraph)."""
+        n = int(e.shape[0]) if n_cells is None else int(n_cells)
+        a = AdvanceArgs(n, int(rho.stride(0)), rho.data_ptr(), e.data_ptr(), float(dt),
+                        _ptr(T_in), _ptr(T_out), _ptr(status), _ptr(newton_iters), _ptr(substeps),
+                        _ptr(failures), None, int(precision), int(lanes))
+        g = C.c_void_p()
+        check(lib().chem_graph_create(self.h, C.byref(a), C.byref(g)))
+        return StepGraph(g)
 
     def lanes(self, precision=FP64):
         v = C.c_int32()

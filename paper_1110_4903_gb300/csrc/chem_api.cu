@@ -384,10 +384,10 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     return CHEM_OK;
 }
 
-// Launch shape of the backward-Euler kernel for (precision, G): warps per
-// block and blocks per SM that maximise resident warps within shared memory
-// and registers.
-static int configure(Handle *h, int prec, int G, LaunchCfg &cfg) {
+// Launch shape of the backward-Euler kernel for (precision, G, warps per
+// block): wpb = 0 picks the warps per block and blocks per SM that maximise
+// resident warps within shared memory and registers.
+int configure(Handle *h, int prec, int G, int wpb_req, LaunchCfg &cfg) {
     const void *fn = prec == CHEM_MIXED ? be_kernel_mixed(G) : be_kernel_fp64(G);
     if (!fn) return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d not available", G);
     const int S = 32 / G;
@@ -400,6 +400,7 @@ static int configure(Handle *h, int prec, int G, LaunchCfg &cfg) {
                                          (int)h->max_smem_optin);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     for (int wpb : {8, 4, 2, 1}) {
+        if (wpb_req && wpb != wpb_req) continue;
         const long long smem = kBlockHeaderBytes + (long long)wpb * S * sb;
         if (smem > h->max_smem_optin) continue;
         int blocks = 0;
@@ -415,8 +416,8 @@ static int configure(Handle *h, int prec, int G, LaunchCfg &cfg) {
         }
     }
     if (best_warps == 0)
-        return fail(CHEM_E_UNSUPPORTED, "one cell slot (%lld bytes) exceeds shared memory at %d lanes/cell",
-                    sb, G);
+        return fail(CHEM_E_UNSUPPORTED, "one cell slot (%lld bytes) exceeds shared memory at %d lanes/cell"
+                    " and %d warps per block", sb, G, wpb_req);
     cfg = best;
     return CHEM_OK;
 }
@@ -430,12 +431,13 @@ int default_lanes(int ns, int prec) {
 }
 
 int get_cfg(Handle *h, int prec, int G, LaunchCfg **out) {
-    const int key = prec * 64 + G;
+    const int wpb = G == h->lanes[prec] ? h->wpb[prec] : 0;
+    const int key = (prec * 64 + G) * 16 + wpb;
     std::lock_guard<std::mutex> lk(h->mu);
     auto it = h->cfgs.find(key);
     if (it == h->cfgs.end()) {
         LaunchCfg c;
-        int rc = configure(h, prec, G, c);
+        int rc = configure(h, prec, G, wpb, c);
         if (rc) return rc;
         it = h->cfgs.emplace(key, c).first;
     }
@@ -514,6 +516,11 @@ int launch_step(Handle *h, const chem_advance_args *a, int prec, int G, unsigned
     LaunchCfg *cfg = nullptr;
     int rc = get_cfg(h, prec, G, &cfg);
     if (rc) return rc;
+    return launch_cfg(h, a, prec, cfg, counter);
+}
+
+int launch_cfg(Handle *h, const chem_advance_args *a, int prec, const LaunchCfg *cfg,
+               unsigned long long *counter) {
     cudaStream_t st = (cudaStream_t)a->stream;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "zeroing the work counter");
@@ -650,6 +657,13 @@ int chem_advance_ex(chem_handle_t hh, const chem_advance_args *a) {
     if (!(a->dt >= 0) || !std::isfinite(a->dt)) return fail(CHEM_E_INVALID_ARG, "dt %g", a->dt);
     const int prec = a->precision < 0 ? h->opts.precision : a->precision;
     if (prec != CHEM_FP64 && prec != CHEM_MIXED) return fail(CHEM_E_INVALID_ARG, "precision %d", prec);
+    if (h->opts.autotune && !h->tuned[prec] && !a->lanes_per_cell) {
+        // first call of this precision: tune on the call's own cells (synchronous)
+        int lanes = 0, wpb = 0;
+        const int rc = chem_autotune(h, prec, a->n_cells, a->ld, a->rho_s, a->e, a->dt, a->T_in, a->stream,
+                                     &lanes, &wpb);
+        if (rc) return rc;
+    }
     int G = a->lanes_per_cell ? a->lanes_per_cell : h->lanes[prec];
     if (G != 2 && G != 4 && G != 8 && G != 16 && G != 32)
         return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d", G);

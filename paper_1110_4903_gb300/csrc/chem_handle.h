@@ -42,6 +42,8 @@ struct chem_handle_s {
     std::atomic<long long> launches{0};
     cudaStream_t stream = nullptr;      // the handle's own stream (host calls, serving)
     int lanes[2] = {0, 0};              // lanes per cell by precision
+    int wpb[2] = {0, 0};                // warps per block by precision (0 = most resident warps)
+    bool tuned[2] = {false, false};     // autotuned already
     std::mutex mu;
     std::map<int, chem::LaunchCfg> cfgs;
     // chem_advance_host staging
@@ -57,7 +59,10 @@ using Handle = ::chem_handle_s;
 int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 int get_cfg(Handle *h, int prec, int G, LaunchCfg **out);
+int configure(Handle *h, int prec, int G, int wpb, LaunchCfg &cfg);
 int launch_step(Handle *h, const chem_advance_args *a, int prec, int G, unsigned long long *counter);
+int launch_cfg(Handle *h, const chem_advance_args *a, int prec, const LaunchCfg *cfg,
+               unsigned long long *counter);
 unsigned long long *next_counter(Handle *h);
 void destroy_serving(Handle *h);
 }  // namespace chem

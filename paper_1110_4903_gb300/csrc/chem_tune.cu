@@ -1,0 +1,179 @@
+// chem_tune.cu -- launch-shape autotuner and captured CUDA graphs of the step.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "../../include/chem.h"
+#include "chem_handle.h"
+
+namespace chem {
+
+// Gathers a strided sample of cells into contiguous buffers.
+__global__ void gather_cells_kernel(int ns, long long m, long long stride, long long ld, const double *rho,
+                                    const double *e, const double *T, double *rho_o, double *e_o,
+                                    double *T_o) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const long long src = i * stride;
+    for (int s = 0; s < ns; ++s) rho_o[(size_t)s * m + i] = rho[(size_t)s * ld + src];
+    e_o[i] = e[src];
+    T_o[i] = T ? T[src] : 1500.0;
+}
+
+}  // namespace chem
+
+using namespace chem;
+
+struct chem_graph_s {
+    Handle *h = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long *counter = nullptr;
+};
+
+extern "C" int chem_autotune(chem_handle_t hh, int32_t prec, int64_t n_cells, int64_t ld, const double *rho_s,
+                             const double *e, double dt, const double *T_in, void *stream, int32_t *lanes_out,
+                             int32_t *wpb_out) {
+    Handle *h = hh;
+    if (!h || !rho_s || !e || n_cells < 1) return fail(CHEM_E_INVALID_ARG, "bad argument");
+    if (prec != CHEM_FP64 && prec != CHEM_MIXED) return fail(CHEM_E_INVALID_ARG, "precision %d", prec);
+    if (ld == 0) ld = n_cells;
+    if (ld < n_cells || !(dt >= 0)) return fail(CHEM_E_INVALID_ARG, "sizes or dt");
+    const int ns = h->ns;
+    const long long m = n_cells < 16384 ? n_cells : 16384;
+    const long long stride = n_cells / m;
+    cudaStream_t st = (cudaStream_t)stream;
+    // pristine sample, work copy, temperature guesses
+    double *buf = nullptr;
+    const size_t per = (size_t)m * (ns + 1);
+    cudaError_t ce = cudaMalloc(&buf, sizeof(double) * (2 * per + m));
+    if (ce != cudaSuccess) return fail(CHEM_E_OOM, "autotune sample buffers");
+    double *s_rho = buf, *s_e = buf + (size_t)m * ns, *w_rho = buf + per, *w_e = w_rho + (size_t)m * ns,
+           *s_T = buf + 2 * per;
+    gather_cells_kernel<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(ns, m, stride, ld, rho_s, e, T_in, s_rho, s_e,
+                                                                    s_T);
+    h->launches.fetch_add(1);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best_G = 0, best_w = 0;
+    float best_ms = 1e30f;
+    const int Gs_small[] = {2, 4, 8, 16};
+    const int Gs_large[] = {8, 16, 32};
+    const bool small = ns + 1 <= 16;
+    const int *Gs = small ? Gs_small : Gs_large;
+    const int nG = small ? 4 : 3;
+    int rc = CHEM_OK;
+    for (int gi = 0; gi < nG && rc == CHEM_OK; ++gi) {
+        for (int wpb : {1, 2, 4, 8}) {
+            LaunchCfg cfg;
+            if (configure(h, prec, Gs[gi], wpb, cfg) != CHEM_OK) continue;   // does not fit
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaMemcpyAsync(w_rho, s_rho, sizeof(double) * per, cudaMemcpyDeviceToDevice, st);
+                chem_advance_args a;
+                memset(&a, 0, sizeof a);
+                a.n_cells = m;
+                a.ld = m;
+                a.rho_s = w_rho;
+                a.e = w_e;
+                a.dt = dt;
+                a.T_in = s_T;
+                a.stream = st;
+                cudaEventRecord(e0, st);
+                rc = launch_cfg(h, &a, prec, &cfg, next_counter(h));
+                cudaEventRecord(e1, st);
+                if (rc) break;
+                ce = cudaEventSynchronize(e1);
+                if (ce != cudaSuccess) { rc = cuda_fail(ce, "autotune run"); break; }
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (rc) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_G = Gs[gi];
+                best_w = wpb;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc) return rc;
+    if (!best_G) return fail(CHEM_E_UNSUPPORTED, "no launch shape fits");
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        h->lanes[prec] = best_G;
+        h->wpb[prec] = best_w;
+        h->tuned[prec] = true;
+    }
+    if (lanes_out) *lanes_out = best_G;
+    if (wpb_out) *wpb_out = best_w;
+    return CHEM_OK;
+}
+
+extern "C" int chem_graph_create(chem_handle_t hh, const chem_advance_args *a, chem_graph_t *out) {
+    Handle *h = hh;
+    if (!h || !a || !out) return fail(CHEM_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (a->n_cells < 1 || !a->rho_s || !a->e || (a->ld != 0 && a->ld < a->n_cells) || !(a->dt >= 0))
+        return fail(CHEM_E_INVALID_ARG, "bad step arguments");
+    const int prec = a->precision < 0 ? h->opts.precision : a->precision;
+    if (prec != CHEM_FP64 && prec != CHEM_MIXED) return fail(CHEM_E_INVALID_ARG, "precision %d", prec);
+    const int G = a->lanes_per_cell ? a->lanes_per_cell : h->lanes[prec];
+    LaunchCfg *cfg = nullptr;
+    int rc = get_cfg(h, prec, G, &cfg);   // resolve attributes before capturing
+    if (rc) return rc;
+    chem_graph_s *g = new chem_graph_s();
+    g->h = h;
+    cudaError_t ce = cudaMalloc(&g->counter, sizeof(unsigned long long));
+    if (ce != cudaSuccess) { delete g; return fail(CHEM_E_OOM, "graph work counter"); }
+    cudaStream_t cs;
+    ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) { cudaFree(g->counter); delete g; return cuda_fail(ce, "capture stream"); }
+    chem_advance_args b = *a;
+    b.stream = cs;
+    ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        rc = launch_step(h, &b, prec, G, g->counter);
+        const cudaError_t ce2 = cudaStreamEndCapture(cs, &g->graph);
+        if (rc == CHEM_OK && ce2 != cudaSuccess) rc = cuda_fail(ce2, "ending the capture");
+    } else {
+        rc = cuda_fail(ce, "beginning the capture");
+    }
+    if (rc == CHEM_OK) {
+        ce = cudaGraphInstantiate(&g->exec, g->graph, 0);
+        if (ce != cudaSuccess) rc = cuda_fail(ce, "instantiating the graph");
+    }
+    cudaStreamDestroy(cs);
+    // the captured launch was counted by launch_step; it has not run
+    h->launches.fetch_sub(1);
+    if (rc) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        cudaFree(g->counter);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return CHEM_OK;
+}
+
+extern "C" int chem_graph_launch(chem_graph_t g, void *stream) {
+    if (!g) return fail(CHEM_E_INVALID_ARG, "graph is NULL");
+    const cudaError_t ce = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "launching the graph");
+    g->h->launches.fetch_add(1);
+    return CHEM_OK;
+}
+
+extern "C" int chem_graph_destroy(chem_graph_t g) {
+    if (!g) return fail(CHEM_E_INVALID_ARG, "graph is NULL");
+    cudaDeviceSynchronize();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->counter) cudaFree(g->counter);
+    delete g;
+    return CHEM_OK;
+}

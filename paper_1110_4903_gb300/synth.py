@@ -388,12 +388,24 @@ def uniform_field(ns: int, n: int, T_lo: float, T_hi: float, seed: int,
     return Field(T=T, P=np.full(n, P), Y=Y)
 
 
-def front_field(ns: int, nx: int = 2048, ny: int = 1024, seed: int = 4,
+def _stable_order(mech):
+    """Species indices from most to least stable per atom by the generator's
+    own formation-enthalpy draw (a6 + 298.15 a1, the same proxy that orients
+    the reactions)."""
+    atoms = mech.elem_comp.sum(1)
+    proxy = (mech.nasa7[:, 0, 5] + 298.15 * mech.nasa7[:, 0, 0]) / atoms
+    return np.argsort(proxy, kind="stable")
+
+
+def front_field(mech, nx: int = 2048, ny: int = 1024, seed: int = 4,
                 P: float = 101325.0, band: int = 64, T_band: float = 2800.0) -> Field:
-    """2-D field, x fastest: 300-1200 K gas with T linear in y plus a smooth
-    seeded perturbation, and a vertical band `band` columns wide at T_band
-    with tanh edges.  Two composition families: one outside the band, one
-    inside it."""
+    """2-D field, x fastest: unburnt gas at 300-1200 K (T linear in y plus a
+    smooth seeded perturbation) and a vertical band `band` columns wide at
+    T_band with tanh edges.  Outside the band the gas is a stable reactant
+    mixture (N2, O2, H2 and the two most stable polyatomic species); inside
+    it is product-rich (the most stable species per atom) with a small
+    radical pool; the edges mix the two."""
+    ns = mech.ns
     rng = np.random.default_rng(seed)
     x = np.arange(nx, dtype=np.float64)[None, :]
     y = np.arange(ny, dtype=np.float64)[:, None]
@@ -406,13 +418,22 @@ def front_field(ns: int, nx: int = 2048, ny: int = 1024, seed: int = 4,
     wgt = 0.5 * (np.tanh((x - (xc - band / 2)) / 4.0) - np.tanh((x - (xc + band / 2)) / 4.0))
     wgt = np.broadcast_to(wgt, (ny, nx))
     T = T_gas * (1.0 - wgt) + T_band * wgt
-    half = rng.permutation(ns)
-    a_out = np.full(ns, 0.2)
-    a_out[half[: ns // 2]] = 4.0
-    a_in = np.full(ns, 0.2)
-    a_in[half[ns // 2:]] = 4.0
-    Y_out = rng.dirichlet(a_out)
-    Y_in = rng.dirichlet(a_in)
+    names = list(mech.species)
+    order = [int(i) for i in _stable_order(mech)]
+    poly = [i for i in order if mech.elem_comp[i].sum() > 2][:2]
+    Y_out = np.zeros(ns)
+    for nm, v in (("N2", 0.70), ("O2", 0.20), ("H2", 0.04)):
+        Y_out[names.index(nm)] = v
+    for i in poly:
+        Y_out[i] += 0.03
+    Y_in = np.zeros(ns)
+    Y_in[names.index("N2")] = 0.70
+    stable = [i for i in order if names[i] != "N2"][:4]
+    Y_in[stable] += rng.dirichlet(np.full(len(stable), 4.0)) * 0.29
+    radicals = [i for i in range(ns) if mech.elem_comp[i].sum() == 1]
+    Y_in[radicals] += 0.01 / len(radicals)
+    Y_out /= Y_out.sum()
+    Y_in /= Y_in.sum()
     w = wgt.reshape(-1)
     Y = Y_out[:, None] * (1.0 - w)[None, :] + Y_in[:, None] * w[None, :]
     return Field(T=T.reshape(-1).copy(), P=np.full(nx * ny, P), Y=np.ascontiguousarray(Y))
@@ -431,7 +452,7 @@ def workload(name: str):
         return m, uniform_field(m.ns, 1 << 18, 900.0, 2800.0, seed=3), 1e-6
     if name == "hc36-front-2M":
         m = hydrocarbon_36sp()
-        return m, front_field(m.ns, seed=4), 1e-6
+        return m, front_field(m, seed=4), 1e-6
     raise KeyError(name)
 
 
