@@ -240,6 +240,97 @@ def time_path(torch, ch, rho0, e0, T_in, dt, precision, steps, warmup, flush, st
     return tot, ker, stats
 
 
+def serving_run(torch, chem, synth, device, n_requests, rate_frac=0.7, budget_bytes=0, seed=5,
+                n_sims=128, max_inflight=8):
+    """Poisson stream of chemistry requests from many simulations (9 or 36
+    species with probability 1/2, 1k-256k cells log-uniform, dt log-uniform
+    1e-8..1e-5 s) against a request server; states are resident on the
+    device.  The rate is rate_frac x the capacity measured by a saturating
+    burst first.  Returns throughput and latency percentiles."""
+    rng = np.random.default_rng(seed)
+    mechs = [synth.h2_air_9sp(), synth.hydrocarbon_36sp()]
+    handles = [chem.Chem(m, precision=chem.MIXED) for m in mechs]
+    sims = []
+    for i in range(n_sims):
+        k = i % 2
+        n = int(np.exp(rng.uniform(np.log(1024), np.log(262144))))
+        f = synth.uniform_field(mechs[k].ns, n, 900.0, 2800.0, seed=10_000 + i)
+        T = torch.tensor(f.T, device=device)
+        rho = torch.empty((mechs[k].ns, n), dtype=torch.float64, device=device)
+        e = torch.empty(n, dtype=torch.float64, device=device)
+        handles[k].state_from_tpy(T, torch.tensor(f.P, device=device),
+                                  torch.tensor(f.Y, device=device), rho, e)
+        sims.append((k, n, rho, e))
+    torch.cuda.synchronize()
+    srv = chem.Server(budget_bytes=budget_bytes, max_inflight=max_inflight)
+    busy = {}
+
+    def pick(k, draw):
+        cands = [i for i in range(n_sims) if sims[i][0] == k and i not in busy]
+        return cands[int(draw * len(cands)) % len(cands)] if cands else None
+
+    def retire():
+        for i, t in list(busy.items()):
+            r = srv.poll(t)
+            if r.state in (chem.REQ_DONE, chem.REQ_FAILED, chem.REQ_CANCELLED):
+                done.append((t, r, sims[i][1]))
+                del busy[i]
+
+    # capacity: a saturating burst
+    done = []
+    t0 = time.perf_counter()
+    burst = 24
+    for j in range(burst):
+        k = j % 2
+        i = pick(k, rng.uniform())
+        busy[i] = srv.submit(handles[k], sims[i][2], sims[i][3],
+                             float(np.exp(rng.uniform(np.log(1e-8), np.log(1e-5)))))
+    while busy:
+        retire()
+        time.sleep(0.0005)
+    cap_rps = burst / (time.perf_counter() - t0)
+    rate = rate_frac * cap_rps
+    # the stream
+    reqs = synth.poisson_requests(n_requests, rate, seed=seed)
+    done = []
+    arrivals = {}
+    cells = 0
+    t_start = time.perf_counter()
+    srv_t0 = None
+    for q in reqs:
+        while time.perf_counter() - t_start < q["t"]:
+            retire()
+            time.sleep(0.0002)
+        i = pick(q["mech"], rng.uniform())
+        while i is None:          # every simulation of this mechanism is in flight
+            retire()
+            time.sleep(0.0002)
+            i = pick(q["mech"], rng.uniform())
+        t = srv.submit(handles[q["mech"]], sims[i][2], sims[i][3], q["dt"])
+        busy[i] = t
+        arrivals[t] = time.perf_counter() - (t_start + q["t"])   # client-side delay
+        cells += sims[i][1]
+    while busy:
+        retire()
+        time.sleep(0.0002)
+    wall = time.perf_counter() - t_start
+    # latency from the scheduled arrival (server clock offset from the submit stamp)
+    lat = []
+    for t, r, n in done:
+        if t in arrivals:
+            lat.append(r.t_done - r.t_submit + max(0.0, arrivals[t]))
+    lat = np.array(lat)
+    st = srv.stats()
+    srv.close()
+    for h in handles:
+        h.close()
+    return {"requests": len(lat), "rate_rps": rate, "capacity_rps": cap_rps, "rate_frac": rate_frac,
+            "cell_updates_per_s": cells / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "budget_bytes": st["budget_bytes"], "max_inflight": max_inflight,
+            "failed": st["failed"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -257,6 +348,10 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="autotune the launch shape first")
     ap.add_argument("--cells", type=int, default=0,
                     help="time the first CELLS cells only (a smaller case for profiling)")
+    ap.add_argument("--serving-requests", type=int, default=120,
+                    help="requests in the serving stream (0: skip the serving run)")
+    ap.add_argument("--serving-rate", type=float, default=0.7, help="load as a fraction of capacity")
+    ap.add_argument("--serving-budget", type=int, default=0, help="server HBM budget in bytes")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_init(args)
@@ -370,6 +465,11 @@ def main():
                "api": "chem_advance_host (pinned host buffers, synchronous), %s" % head_name,
                "steps": len(times)}
 
+    serving = None
+    if args.serving_requests > 0 and not args.cells:
+        serving = serving_run(torch, chem, synth, device, args.serving_requests, args.serving_rate,
+                              args.serving_budget)
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
@@ -393,7 +493,7 @@ def main():
                 "newton_iters_mean": hr["newton_iters_mean"],
                 "newton_iters_max": hr["newton_iters_max"], "cells_ok": hr["cells_ok"],
                 "roofline": hr["roofline"], "cpu_baseline": cb, "e2e": e2e,
-                "gpu_launches": gpu_launches, "clocks": clk}
+                "gpu_launches": gpu_launches, "clocks": clk, "serving": serving}
         for name, r in results.items():
             line[name] = {k: v for k, v in r.items()}
         if "fp64" in results and "mixed" in results:

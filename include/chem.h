@@ -210,6 +210,77 @@ int chem_get_lanes_per_cell(chem_handle_t h, int32_t precision, int32_t *lanes);
 /* Kernel launches this handle has issued since creation (all entry points). */
 int chem_launch_count(chem_handle_t h, int64_t *count);
 
+/* ---- serving: continuous batching of requests from many simulations ----
+ * A server owns a scheduler thread, max_inflight CUDA streams and a device
+ * pool of hbm_budget_bytes.  chem_submit queues a request (its own mechanism
+ * handle, cell count, dt and state); the scheduler admits the head of the
+ * FIFO queue as soon as a stream is free and the request's bytes
+ * (n_cells * (8 N_s + 20) + 1024) fit in the remaining budget, and runs it
+ * on that stream, so requests admitted while others run overlap with them
+ * on the device.  Device-resident states (host = 0) are stepped in place and
+ * count against the budget while in flight; host states (host = 1) are
+ * copied through the pool and back.  A request is computed exactly as by
+ * chem_advance_ex with the same handle, whatever else is in flight.
+ * Requests larger than the whole budget are refused (CHEM_E_OVER_BUDGET).
+ * Handles must outlive their requests. */
+#define CHEM_REQ_QUEUED    0
+#define CHEM_REQ_RUNNING   1
+#define CHEM_REQ_DONE      2
+#define CHEM_REQ_FAILED    3
+#define CHEM_REQ_CANCELLED 4
+
+typedef struct chem_server_s *chem_server_t;
+
+typedef struct chem_server_options {
+    int64_t hbm_budget_bytes;   /* device pool and in-flight budget; 0 = a quarter of free memory */
+    int32_t max_inflight;       /* requests running at once (streams), 1..64; default 8 */
+    int32_t queue_capacity;     /* queued requests before chem_submit refuses; default 100000 */
+} chem_server_options;
+
+typedef struct chem_request {
+    chem_handle_t mech;         /* mechanism and options of this request */
+    int64_t  n_cells;
+    int64_t  ld;                /* 0 = n_cells */
+    double  *rho_s;             /* state, device (host = 0) or host (host = 1), in/out */
+    double  *e;
+    int32_t  host;
+    int32_t  precision;         /* -1 = the handle's */
+    double   dt;
+    double  *T_out;             /* optional, same memory kind as the state */
+    int32_t *status;            /* optional, same memory kind as the state */
+    void    *ready_event;       /* optional cudaEvent_t: the request's stream waits for it
+                                   before touching device buffers (e.g. recorded after the
+                                   writes that produced the state); the event must stay
+                                   valid until the request has started */
+} chem_request;
+
+typedef struct chem_result {
+    int32_t state;              /* CHEM_REQ_* */
+    int32_t error;              /* CHEM_E_* when FAILED */
+    double  t_submit, t_start, t_done;   /* seconds on the server's monotonic clock */
+} chem_result;
+
+typedef struct chem_server_stats_t {
+    int64_t queued, running, completed, failed;
+    int64_t bytes_in_use, budget_bytes, launches;
+} chem_server_stats_t;
+
+int chem_server_default_options(chem_server_options *o);
+int chem_server_create(const chem_server_options *o, chem_server_t *out);
+/* Cancels queued requests, waits for running ones, frees the server. */
+int chem_server_destroy(chem_server_t s);
+int chem_submit(chem_server_t s, const chem_request *r, uint64_t *ticket);
+/* Non-blocking state of a request. */
+int chem_poll(chem_server_t s, uint64_t ticket, chem_result *out);
+/* Waits until the request finishes or timeout_us passes (< 0: no limit);
+ * CHEM_E_TIMEOUT with the current state in *out when it runs out. */
+int chem_wait(chem_server_t s, uint64_t ticket, int64_t timeout_us, chem_result *out);
+/* Cancels a request that is still queued (its state is never touched). */
+int chem_cancel(chem_server_t s, uint64_t ticket);
+/* Forgets a finished request's record. */
+int chem_release(chem_server_t s, uint64_t ticket);
+int chem_server_stats(chem_server_t s, chem_server_stats_t *out);
+
 /* Human-readable text for a CHEM_E_* code (static storage). */
 const char *chem_strerror(int code);
 

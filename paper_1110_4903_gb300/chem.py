@@ -51,6 +51,31 @@ class AdvanceArgs(C.Structure):
                 ("lanes_per_cell", C.c_int32)]
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_inflight", C.c_int32),
+                ("queue_capacity", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("mech", C.c_void_p), ("n_cells", C.c_int64), ("ld", C.c_int64),
+                ("rho_s", C.c_void_p), ("e", C.c_void_p), ("host", C.c_int32),
+                ("precision", C.c_int32), ("dt", C.c_double), ("T_out", C.c_void_p),
+                ("status", C.c_void_p), ("ready_event", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("running", C.c_int64), ("completed", C.c_int64),
+                ("failed", C.c_int64), ("bytes_in_use", C.c_int64), ("budget_bytes", C.c_int64),
+                ("launches", C.c_int64)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
+
 _lib = None
 
 
@@ -79,6 +104,15 @@ def lib():
             "chem_graph_create": [p, p, p],
             "chem_graph_launch": [p, p],
             "chem_graph_destroy": [p],
+            "chem_server_default_options": [p],
+            "chem_server_create": [p, p],
+            "chem_server_destroy": [p],
+            "chem_submit": [p, p, p],
+            "chem_poll": [p, C.c_uint64, p],
+            "chem_wait": [p, C.c_uint64, i64, p],
+            "chem_cancel": [p, C.c_uint64],
+            "chem_release": [p, C.c_uint64],
+            "chem_server_stats": [p, p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -243,3 +277,85 @@ class Chem:
         v = C.c_int64()
         check(lib().chem_launch_count(self.h, C.byref(v)))
         return v.value
+
+
+class Server:
+    """Request server (chem_server_*): continuous batching of chemistry steps."""
+
+    def __init__(self, budget_bytes=0, max_inflight=8, queue_capacity=100000):
+        o = ServerOptions()
+        check(lib().chem_server_default_options(C.byref(o)))
+        o.hbm_budget_bytes = int(budget_bytes)
+        o.max_inflight = int(max_inflight)
+        o.queue_capacity = int(queue_capacity)
+        s = C.c_void_p()
+        check(lib().chem_server_create(C.byref(o), C.byref(s)))
+        self.s = s
+        self._events = {}
+
+    def submit(self, ch, rho, e, dt, *, n_cells=None, host=False, precision=-1, T_out=None,
+               status=None, stream=None):
+        """rho/e: torch device tensors (host=False) or numpy host arrays
+        (host=True).  Device requests wait for an event recorded now on
+        `stream` (default: the current stream), so work queued there before
+        the submit -- e.g. the writes that produced the state -- is finished
+        before the request reads its buffers."""
+        ev = None
+        if host:
+            n = e.shape[0] if n_cells is None else n_cells
+            r = Request(ch.h, n, rho.shape[1], rho.ctypes.data, e.ctypes.data, 1, int(precision),
+                        float(dt), None if T_out is None else T_out.ctypes.data,
+                        None if status is None else status.ctypes.data, None)
+        else:
+            import torch
+            ev = torch.cuda.Event()
+            ev.record(stream if stream is not None else torch.cuda.current_stream())
+            n = int(e.shape[0]) if n_cells is None else int(n_cells)
+            r = Request(ch.h, n, int(rho.stride(0)), rho.data_ptr(), e.data_ptr(), 0, int(precision),
+                        float(dt), _ptr(T_out), _ptr(status), C.c_void_p(ev.cuda_event))
+        t = C.c_uint64()
+        check(lib().chem_submit(self.s, C.byref(r), C.byref(t)))
+        if ev is not None:
+            self._events[t.value] = ev      # kept alive until the request is finished
+        return t.value
+
+    def _finished(self, ticket, r):
+        if r.state in (REQ_DONE, REQ_FAILED, REQ_CANCELLED):
+            self._events.pop(ticket, None)
+        return r
+
+    def poll(self, ticket):
+        r = Result()
+        check(lib().chem_poll(self.s, C.c_uint64(ticket), C.byref(r)))
+        return self._finished(ticket, r)
+
+    def wait(self, ticket, timeout_us=-1):
+        r = Result()
+        rc = lib().chem_wait(self.s, C.c_uint64(ticket), int(timeout_us), C.byref(r))
+        if rc == -6:
+            return None
+        check(rc)
+        return self._finished(ticket, r)
+
+    def cancel(self, ticket):
+        check(lib().chem_cancel(self.s, C.c_uint64(ticket)))
+
+    def release(self, ticket):
+        check(lib().chem_release(self.s, C.c_uint64(ticket)))
+
+    def stats(self):
+        st = ServerStats()
+        check(lib().chem_server_stats(self.s, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            check(lib().chem_server_destroy(self.s))
+            self.s = None
+            self._events.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
