@@ -129,25 +129,13 @@ class Clocks:
 
 
 def dist_init(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        import torch
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        dist.init_process_group(backend)
-    return world, rank, local
+    from paper_1110_4903_gb300 import replicas
+    return replicas.init()
 
 
 def barrier_max(world, value, device):
-    if world == 1:
-        return value
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1110_4903_gb300 import replicas
+    return replicas.max_over_ranks(value, device) if world > 1 else value
 
 
 def cpu_baseline(sample_cells=4096, threads=None):

@@ -281,6 +281,31 @@ int chem_cancel(chem_server_t s, uint64_t ticket);
 int chem_release(chem_server_t s, uint64_t ticket);
 int chem_server_stats(chem_server_t s, chem_server_stats_t *out);
 
+/* ---- batched dense solves: the kinetics-only experiment of Sec. 5.2 ----
+ * Solves n_sys independent systems A_k x_k = b_k of size n (1..CHEM_LU_MAX_N)
+ * in place by Gaussian elimination with row partial pivoting (ties to the
+ * lowest row) in FP64; every arithmetic step of the factorisation is
+ * explicitly rounded and in the scalar order (multiplier a_ij / a_jj, update
+ * a_ik - l a_jk without contraction), so the factors and pivots equal a
+ * scalar elimination bit for bit; x equals the row-by-row substitutions bit
+ * for bit (CHEM_LU_GLOBAL) or to rounding (CHEM_LU_ONCHIP, which runs the
+ * back substitution by columns across the warp).  On return A holds L (unit, below the
+ * diagonal) and U, b holds x, pivots[k*n + j] (optional) the row swapped
+ * into row j, info[k] (optional) 0 or 1 + the first column with a zero or
+ * non-finite pivot.  Layout and kernel by method:
+ *   CHEM_LU_GLOBAL  A[(i*n + j)*n_sys + k], b[i*n_sys + k] (interleaved);
+ *                   one thread per system, the matrices stay in HBM (the
+ *                   paper's global-memory approach).
+ *   CHEM_LU_ONCHIP  A[(k*n + i)*n + j], b[k*n + i] (contiguous); one warp
+ *                   per system, the matrix in shared memory
+ *                   (CHEM_E_UNSUPPORTED when n*(n+1) doubles do not fit).
+ * Device pointers; asynchronous on `stream`. */
+#define CHEM_LU_GLOBAL 0
+#define CHEM_LU_ONCHIP 1
+#define CHEM_LU_MAX_N  256
+int chem_batched_solve(int32_t method, int32_t n, int64_t n_sys, double *A, double *b,
+                       int32_t *pivots, int32_t *info, void *stream);
+
 /* Human-readable text for a CHEM_E_* code (static storage). */
 const char *chem_strerror(int code);
 

@@ -75,6 +75,7 @@ class ServerStats(C.Structure):
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
+LU_GLOBAL, LU_ONCHIP = 0, 1
 
 _lib = None
 
@@ -113,6 +114,7 @@ def lib():
             "chem_cancel": [p, C.c_uint64],
             "chem_release": [p, C.c_uint64],
             "chem_server_stats": [p, p],
+            "chem_batched_solve": [i32, i32, i64, p, p, p, p, p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -359,3 +361,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def batched_solve(method, A, b, pivots=None, info=None, stream=None):
+    """In-place batched solve of device tensors (chem_batched_solve):
+    LU_GLOBAL: A [n, n, n_sys], b [n, n_sys]; LU_ONCHIP: A [n_sys, n, n], b [n_sys, n]."""
+    if method == LU_GLOBAL:
+        n, n_sys = int(A.shape[0]), int(A.shape[2])
+    else:
+        n_sys, n = int(A.shape[0]), int(A.shape[1])
+    check(lib().chem_batched_solve(int(method), n, n_sys, A.data_ptr(), b.data_ptr(), _ptr(pivots),
+                                   _ptr(info), _stream_ptr(stream)))
