@@ -143,6 +143,14 @@ typedef struct chem_advance_args {
 /* chem_advance with strides, temperature guesses and per-cell outputs. */
 int chem_advance_ex(chem_handle_t h, const chem_advance_args *a);
 
+/* Domain-segmented execution (Sec. 5.2): the same step as chem_advance_ex,
+ * issued as consecutive launches over segments of at most segment_cells
+ * cells (the paper called its kernel on segments of the grid to cap the
+ * memory of per-cell Jacobians).  Results are those of one launch, bit for
+ * bit; only the launch granularity changes.  segment_cells <= 0 means one
+ * segment. */
+int chem_advance_segmented(chem_handle_t h, const chem_advance_args *a, int64_t segment_cells);
+
 /* Same step on HOST buffers (rho_s [N_s*ld], e, optional T_out/status):
  * copies to library-owned device buffers, advances, copies back and
  * synchronizes.  Pinned host memory makes the copies faster. */
@@ -203,6 +211,11 @@ typedef struct chem_graph_s *chem_graph_t;
 int chem_graph_create(chem_handle_t h, const chem_advance_args *a, chem_graph_t *out);
 int chem_graph_launch(chem_graph_t g, void *stream);
 int chem_graph_destroy(chem_graph_t g);
+
+/* Formation energies e_f,s = e_s(298.15 K) per unit mass (J/kg) the handle
+ * uses (Eq. 3 leaves them out of e; U = e + sum_s rho_s e_f,s is what a step
+ * conserves).  e_f is a host array of N_s doubles. */
+int chem_formation_energies(chem_handle_t h, double *e_f);
 
 /* Lanes per cell the handle uses for `precision` (after autotuning, if on). */
 int chem_get_lanes_per_cell(chem_handle_t h, int32_t precision, int32_t *lanes);

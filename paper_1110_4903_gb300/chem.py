@@ -94,12 +94,14 @@ def lib():
             "chem_destroy": [p],
             "chem_advance": [p, i64, p, p, d, p],
             "chem_advance_ex": [p, p],
+            "chem_advance_segmented": [p, p, i64],
             "chem_advance_host": [p, i64, i64, p, p, d, p, p],
             "chem_advance_host_static": [p, i64, i64, p, p, d, p, p],
             "chem_static_scratch_bytes": [p],
             "chem_state_from_tpy": [p, i64, i64, p, p, p, p, p, p],
             "chem_temperature": [p, i64, i64, p, p, p, p, p],
             "chem_get_lanes_per_cell": [p, i32, p],
+            "chem_formation_energies": [p, p],
             "chem_launch_count": [p, p],
             "chem_autotune": [p, i32, i64, i64, p, p, d, p, p, p, p],
             "chem_graph_create": [p, p, p],
@@ -219,6 +221,16 @@ class Chem:
                         _ptr(failures), _stream_ptr(stream), int(precision), int(lanes))
         check(lib().chem_advance_ex(self.h, C.byref(a)))
 
+    def advance_segmented(self, rho, e, dt, segment_cells, *, n_cells=None, T_in=None, T_out=None,
+                          status=None, precision=-1, stream=None):
+        """chem_advance_segmented: the same step in launches of at most
+        segment_cells cells."""
+        n = int(e.shape[0]) if n_cells is None else int(n_cells)
+        a = AdvanceArgs(n, int(rho.stride(0)), rho.data_ptr(), e.data_ptr(), float(dt),
+                        _ptr(T_in), _ptr(T_out), _ptr(status), None, None, None,
+                        _stream_ptr(stream), int(precision), 0)
+        check(lib().chem_advance_segmented(self.h, C.byref(a), int(segment_cells)))
+
     def advance_simple(self, n_cells, rho, e, dt, stream=None):
         check(lib().chem_advance(self.h, int(n_cells), rho.data_ptr(), e.data_ptr(), float(dt),
                                  _stream_ptr(stream)))
@@ -269,6 +281,12 @@ class Chem:
         g = C.c_void_p()
         check(lib().chem_graph_create(self.h, C.byref(a), C.byref(g)))
         return StepGraph(g)
+
+    def formation_energies(self):
+        """e_f,s = e_s(298.15 K), J/kg, as the library uses them."""
+        out = np.zeros(self.ns)
+        check(lib().chem_formation_energies(self.h, out.ctypes.data))
+        return out
 
     def lanes(self, precision=FP64):
         v = C.c_int32()

@@ -616,6 +616,8 @@ int chem_create(const chem_mech_desc *mech, const chem_options *opts, chem_handl
     h->max_smem_optin = (long long)prop.sharedMemPerBlockOptin;
     HostTables t;
     build_tables(mech, t);
+    h->ef_host.resize(h->ns);
+    for (int s = 0; s < h->ns; ++s) h->ef_host[s] = t.sp[s * kSpStride + 3];
     rc = upload(t, h->ns, h->nr, h);
     if (rc) { chem_destroy(h); return rc; }
     e = cudaMalloc(&h->counters, sizeof(unsigned long long) * kCounterRing);
@@ -668,6 +670,29 @@ int chem_advance_ex(chem_handle_t hh, const chem_advance_args *a) {
     if (G != 2 && G != 4 && G != 8 && G != 16 && G != 32)
         return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d", G);
     return launch_step(h, a, prec, G, next_counter(h));
+}
+
+int chem_advance_segmented(chem_handle_t hh, const chem_advance_args *a, int64_t segment_cells) {
+    Handle *h = hh;
+    if (!h || !a) return fail(CHEM_E_INVALID_ARG, "NULL handle or arguments");
+    if (segment_cells <= 0 || segment_cells >= a->n_cells) return chem_advance_ex(h, a);
+    const int64_t ld = a->ld > 0 ? a->ld : a->n_cells;
+    for (int64_t off = 0; off < a->n_cells; off += segment_cells) {
+        chem_advance_args s = *a;
+        s.n_cells = std::min<int64_t>(segment_cells, a->n_cells - off);
+        s.ld = ld;
+        s.rho_s = a->rho_s + off;
+        s.e = a->e + off;
+        s.T_in = a->T_in ? a->T_in + off : nullptr;
+        s.T_out = a->T_out ? a->T_out + off : nullptr;
+        s.status = a->status ? a->status + off : nullptr;
+        s.newton_iters = a->newton_iters ? a->newton_iters + off : nullptr;
+        s.substeps = a->substeps ? a->substeps + off : nullptr;
+        s.failures = a->failures ? a->failures + off : nullptr;
+        const int rc = chem_advance_ex(h, &s);
+        if (rc) return rc;
+    }
+    return CHEM_OK;
 }
 
 int chem_advance(chem_handle_t h, int64_t n_cells, double *rho_s, double *e, double dt, void *stream) {
@@ -765,6 +790,13 @@ int chem_temperature(chem_handle_t hh, int64_t n, int64_t ld, const double *rho_
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return cuda_fail(ce, "temperature launch");
     h->launches.fetch_add(1);
+    return CHEM_OK;
+}
+
+int chem_formation_energies(chem_handle_t hh, double *e_f) {
+    Handle *h = hh;
+    if (!h || !e_f) return fail(CHEM_E_INVALID_ARG, "NULL argument");
+    for (int s = 0; s < h->ns; ++s) e_f[s] = h->ef_host[s];
     return CHEM_OK;
 }
 

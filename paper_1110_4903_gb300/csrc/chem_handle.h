@@ -6,6 +6,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "../../include/chem.h"
 #include "chem_internal.h"
@@ -51,6 +52,7 @@ struct chem_handle_s {
     void *host_rho = nullptr;
     size_t host_bytes = 0;
     chem::ServingState *serving = nullptr;
+    std::vector<double> ef_host;        // formation energies per unit mass
 };
 
 namespace chem {

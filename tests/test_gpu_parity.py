@@ -186,3 +186,23 @@ def test_full_size_sampled(torch, wl, sample):
     P.compare(rho[:, idx].cpu().numpy(), e[idx].cpu().numpy(), og, rr, er, oo, r0, P.TOL_FP64,
               min_same=0.95, flip_tol=1e-3)
     c.close()
+
+
+@pytest.mark.parametrize("wl,ncell,dt", [("h2air-1k", 1024, 1e-7), ("hc36-256k", 128, 1e-9)])
+def test_point_implicit_mode(torch, wl, ncell, dt):
+    """The scheme exactly as printed (Eq. 29, one linearised step per
+    substep, no Newton iteration): GPU against the oracle's same mode.  (On
+    the 36-species field at dt = 1e-6 s one linearised step is so
+    ill-conditioned that most cells fail the positivity check either way;
+    1e-9 s keeps the linear step meaningful.)"""
+    from paper_1110_4903_gb300 import chem
+    m, f, _ = synth.workload(wl)
+    fs = synth.subsample(f, np.arange(ncell) * 131 % f.n)
+    rho, e = P.initial_state(m, fs)
+    opts = dict(point_implicit=1, max_newton=1, max_halvings=0)
+    c = chem.Chem(m, **opts)
+    rr, er, oo = P.oracle_reference(m, rho, e, dt, fs.T, threads=THREADS, **opts)
+    rg, eg, og = P.gpu_run(torch, c, rho, e, dt, T_in=fs.T)
+    assert (og["newton_iters"][oo["status"] == 0] == 1).all()
+    P.compare(rg, eg, og, rr, er, oo, rho, P.TOL_FP64, min_same=1.0)
+    c.close()

@@ -77,3 +77,18 @@ def test_graph_steps_match_plain_steps(torch, front):
     assert (st == 0).all()
     g.close()
     c.close()
+
+
+def test_segmented_equals_single_launch(torch, front):
+    from paper_1110_4903_gb300 import chem
+    m, fs, rho, e, dt = front
+    dev = torch.device("cuda")
+    c = chem.Chem(m, precision=chem.MIXED)
+    r1, e1 = torch.tensor(rho, device=dev), torch.tensor(e, device=dev)
+    c.advance(r1, e1, dt)
+    for seg in (4096, 5000, 32768):
+        r2, e2 = torch.tensor(rho, device=dev), torch.tensor(e, device=dev)
+        c.advance_segmented(r2, e2, dt, seg)
+        torch.cuda.synchronize()
+        assert torch.equal(r1, r2) and torch.equal(e1, e2), seg
+    c.close()
