@@ -98,12 +98,15 @@ typedef struct chem_options {
     int64_t hbm_budget_bytes; /* serving: device bytes requests may hold (0 = 50% of free) */
     int32_t max_newton_mixed; /* Newton iterations per attempt on the CHEM_MIXED path, whose
                                  FP32 LU makes convergence linear; 1..1000 */
+    double  conv_kappa;       /* > 0: also converged when the contraction theta = norm_k/norm_k-1 < 1
+                                 bounds the remaining error, theta/(1-theta) norm_k <= conv_kappa
+                                 (Hairer & Wanner's stopping estimate); 0 = off; 0..1 */
 } chem_options;
 
 /* Fills *o with the defaults: FP64, rtol 1e-10, atol_rel 1e-12,
  * max_newton 12, max_halvings 20, max_attempts 1000, point_implicit 0,
  * div_check 1, lanes_per_cell 0, autotune 0, hbm_budget_bytes 0,
- * max_newton_mixed 12. */
+ * max_newton_mixed 12, conv_kappa 0.01. */
 int chem_default_options(chem_options *o);
 
 /* Validates the mechanism (index ranges, 1..3 species per side with
@@ -318,6 +321,13 @@ int chem_server_stats(chem_server_t s, chem_server_stats_t *out);
 #define CHEM_LU_MAX_N  256
 int chem_batched_solve(int32_t method, int32_t n, int64_t n_sys, double *A, double *b,
                        int32_t *pivots, int32_t *info, void *stream);
+
+/* Diagnostics: evaluates the step kernel's own exp (table-driven, after
+ * Tang) and reciprocal (rcp.approx + two Newton steps) at n device points x,
+ * next to CUDA's exp and IEEE division, for tests of their error.
+ * Synchronous. */
+int chem_selftest_math(int64_t n, const double *x, double *y_exp, double *y_exp_ref,
+                       double *y_rcp, double *y_rcp_ref, void *stream);
 
 /* Human-readable text for a CHEM_E_* code (static storage). */
 const char *chem_strerror(int code);

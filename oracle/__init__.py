@@ -52,7 +52,7 @@ class Opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol_rel", C.c_double),
                 ("max_newton", C.c_int), ("max_halvings", C.c_int),
                 ("max_attempts", C.c_int), ("point_implicit", C.c_int),
-                ("div_check", C.c_int)]
+                ("div_check", C.c_int), ("conv_kappa", C.c_double)]
 
 
 class _CellResult(C.Structure):

@@ -434,7 +434,12 @@ void om_lu_solve(int n, const double *LU, const int *piv, double *b)
 /* ---------------------------------------------------------------------------
  * Backward Euler over one (sub)step h, Eq. 29 iterated to convergence:
  *   F(x) = x - x0 - h Omega(x),   (I - h J(x)) delta = -F(x),   x <- x + delta,
- * converged when max_i |delta_i| / (rtol |x_i| + atol_i) <= 1.
+ * converged when max_i |delta_i| / (rtol |x_i| + atol_i) <= 1, or (with
+ * conv_kappa > 0) when the observed contraction theta = norm_k / norm_(k-1) < 1
+ * bounds the error still left, theta / (1 - theta) norm_k <= conv_kappa: the
+ * stopping estimate of simplified Newton in Hairer & Wanner, Solving ODEs II,
+ * Sec. IV.8, with their safety factor.  A factor well below 1 keeps the
+ * accepted update small enough that its rounding stays below the tolerance.
  * The first iteration uses T0 = T(x0); later ones recover T at the iterate
  * with the previous T as the guess.  A converged state is accepted only if its
  * temperature is recoverable and no density is below -atol.
@@ -489,6 +494,11 @@ static int be_substep(const om_mech *m, const om_opts *o, const double *x0, doub
             ok = 1;
             break;
         }
+        if (o->conv_kappa > 0.0 && k >= 1 && norm < norm_prev &&
+            norm / norm_prev / (1.0 - norm / norm_prev) * norm <= o->conv_kappa) {
+            ok = 1;
+            break;
+        }
         if (o->div_check && k >= 2 && norm >= norm_prev)
             goto done;
         norm_prev = norm;
@@ -520,6 +530,7 @@ void om_default_opts(om_opts *o)
     o->max_attempts = 1000;
     o->point_implicit = 0;
     o->div_check = 1;
+    o->conv_kappa = 0.01;
 }
 
 /* ---------------------------------------------------------------------------

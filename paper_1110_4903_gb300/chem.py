@@ -40,7 +40,8 @@ class Options(C.Structure):
                 ("max_newton", C.c_int32), ("max_halvings", C.c_int32), ("max_attempts", C.c_int32),
                 ("point_implicit", C.c_int32), ("div_check", C.c_int32),
                 ("lanes_per_cell", C.c_int32), ("autotune", C.c_int32),
-                ("hbm_budget_bytes", C.c_int64), ("max_newton_mixed", C.c_int32)]
+                ("hbm_budget_bytes", C.c_int64), ("max_newton_mixed", C.c_int32),
+                ("conv_kappa", C.c_double)]
 
 
 class AdvanceArgs(C.Structure):
@@ -117,6 +118,7 @@ def lib():
             "chem_release": [p, C.c_uint64],
             "chem_server_stats": [p, p],
             "chem_batched_solve": [i32, i32, i64, p, p, p, p, p],
+            "chem_selftest_math": [i64, p, p, p, p, p, p],
         }
         for name, args in sig.items():
             f = getattr(L, name)

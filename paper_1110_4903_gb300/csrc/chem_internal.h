@@ -44,7 +44,7 @@ constexpr int kRxnFStride = 2;
 constexpr int kChunk = 8;
 
 // Entries of the exp table (2^(j/kExpTab)).
-constexpr int kExpTab = 64;
+constexpr int kExpTab = 256;
 
 // D entries: one per (reaction r, species k) pair whose concentration the
 // progress rate Q_r depends on, holding dQ_r/drho_k without the all-ones
@@ -87,7 +87,7 @@ struct DeviceMech {
 };
 
 struct StepOptions {
-    double rtol, atol_rel;
+    double rtol, atol_rel, conv_kappa;
     int max_newton, max_halvings, max_attempts, point_implicit, div_check;
 };
 
@@ -109,8 +109,9 @@ struct StepBatch {
 enum CellStatus { kCellOk = 0, kCellNewtonFailed = 1, kCellTFailed = 2, kCellBadInput = 3,
                   kCellTooManySteps = 4 };
 
-// Shared memory: a block header (the exp table) then one region per cell slot.
-constexpr int kBlockHeaderBytes = kExpTab * 8;
+// Shared memory of a block: one region per cell slot (no block header; the
+// exp table is read through L1).
+constexpr int kBlockHeaderBytes = 0;
 
 // The D region of a slot holds the nD D entries (Jacobian type) and, earlier
 // in each Newton iteration, the species-gather partial sums (3 doubles per

@@ -95,26 +95,27 @@ __device__ __forceinline__ double frcp(double a) {
 __device__ __forceinline__ float frcp(float a) { return __frcp_rn(a); }
 
 // exp by the table-driven reduction of P. T. P. Tang, ACM TOMS 15(2), 1989:
-// x = (64 k + j) ln2/64 + r with |r| <= ln2/128, exp(x) = 2^k 2^(j/64) e^r,
-// 2^(j/64) from a 64-entry table and e^r - 1 by its degree-5 Taylor
-// polynomial (truncation below 4e-17 on that interval).  |x| > 700 (and NaN)
-// falls back to the library exp.
+// x = (256 k + j) ln2/256 + r with |r| <= ln2/512, exp(x) = 2^k 2^(j/256) e^r,
+// 2^(j/256) from a 256-entry table and e^r - 1 by its degree-4 Taylor
+// polynomial (truncation below 4e-17 on that interval): nine FP64
+// operations.  |x| >= 512, infinities and NaN (decided on the exponent bits,
+// no FP64 compare) fall back to the library exp.
 __device__ __forceinline__ double fexp(double x, const double *tab) {
-    if (!(fabs(x) <= 700.0)) return exp(x);
+    const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
+    if (((hi >> 20) & 0x7ffu) > 0x407u) return exp(x);
     const double kShift = 6755399441055744.0;               // 1.5 * 2^52
-    const double t = fma(x, 92.33248261689366, kShift);     // x * 64/ln2, rounded
+    const double t = fma(x, 369.3299304675746, kShift);     // x * 256/ln2, rounded
     const int n = (int)(unsigned)__double_as_longlong(t);
     const double nd = t - kShift;
-    double r = fma(nd, -0x1.62e42fefa0000p-7, x);            // ln2/64, high 36 bits
-    r = fma(nd, -0x1.cf79abc9e3b3ap-46, r);                  // ln2/64, low part
-    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    p = fma(r, p, 1.0 / 6.0);
+    double r = fma(nd, -0x1.62e42fefa0000p-9, x);            // ln2/256, high 36 bits
+    r = fma(nd, -0x1.cf79abc9e3b3ap-48, r);                  // ln2/256, low part
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     p = fma(r, p, 0.5);
     p = fma(r, p, 1.0);
     p *= r;                                                  // e^r - 1
-    const double s = tab[n & (kExpTab - 1)];
+    const double s = __ldg(tab + (n & (kExpTab - 1)));
     const double y = fma(s, p, s);
-    const long long k = (long long)(n >> 6);
+    const long long k = (long long)(n >> 8);
     return __longlong_as_double(__double_as_longlong(y) + (k << 52));
 }
 
@@ -527,11 +528,10 @@ __global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, St
     const int slot = lane / G;
     const int sl = lane - slot * G;
     const int ns = m.ns, n = ns + 1;
-    double *tab = reinterpret_cast<double *>(smem);
-    for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) tab[i] = m.exp_tab[i];
+    const double *tab = m.exp_tab;   // 2 KB, stays in L1
     const long long sbytes = slot_bytes_for(ns, m.nr, m.nD, m.n_items, (int)sizeof(JT));
     SlotMem<JT> sm;
-    sm.carve(smem + kBlockHeaderBytes + (size_t)(warp * S + slot) * sbytes, m);
+    sm.carve(smem + (size_t)(warp * S + slot) * sbytes, m);
     // sentinel species: concentration 1, no Gibbs or enthalpy contribution
     if (sl == 0) {
         sm.c[ns] = 1.0;
@@ -707,7 +707,9 @@ __global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, St
             ++iters;
             if (bad) {
                 substep_fail();
-            } else if (o.point_implicit || norm <= 1.0) {
+            } else if (o.point_implicit || norm <= 1.0 ||
+                       (o.conv_kappa > 0.0 && k >= 1 && norm < norm_prev &&
+                        norm / norm_prev / (1.0 - norm / norm_prev) * norm <= o.conv_kappa)) {
                 state = kCheckT;
             } else if (o.div_check && k >= 2 && norm >= norm_prev) {
                 substep_fail();

@@ -1,0 +1,49 @@
+// chem_selftest.cu -- diagnostics: the step kernel's own exp and reciprocal
+// evaluated next to CUDA's, so tests can bound their error.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/chem.h"
+#include "chem_handle.h"
+#include "chem_kernel.cuh"
+
+namespace chem {
+
+__global__ void selftest_kernel(long long n, const double *x, const double *tab_g, double *y_exp,
+                                double *y_exp_ref, double *y_rcp, double *y_rcp_ref) {
+    const double *tab = tab_g;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    y_exp[i] = fexp(v, tab);
+    y_exp_ref[i] = exp(v);
+    y_rcp[i] = frcp(v);
+    y_rcp_ref[i] = 1.0 / v;
+}
+
+}  // namespace chem
+
+using namespace chem;
+
+extern "C" int chem_selftest_math(int64_t n, const double *x, double *y_exp, double *y_exp_ref, double *y_rcp,
+                                  double *y_rcp_ref, void *stream) {
+    if (n < 0 || !x || !y_exp || !y_exp_ref || !y_rcp || !y_rcp_ref)
+        return fail(CHEM_E_INVALID_ARG, "NULL argument");
+    if (n == 0) return CHEM_OK;
+    std::vector<double> tab(kExpTab);
+    for (int j = 0; j < kExpTab; ++j) tab[j] = (double)std::exp2l((long double)j / kExpTab);
+    double *d_tab = nullptr;
+    cudaError_t ce = cudaMalloc(&d_tab, sizeof(double) * kExpTab);
+    if (ce != cudaSuccess) return fail(CHEM_E_OOM, "self-test table");
+    ce = cudaMemcpy(d_tab, tab.data(), sizeof(double) * kExpTab, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+        selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, x, d_tab, y_exp, y_exp_ref,
+                                                                                      y_rcp, y_rcp_ref);
+        ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize((cudaStream_t)stream);
+    }
+    cudaFree(d_tab);
+    if (ce != cudaSuccess) return cuda_fail(ce, "self-test");
+    return CHEM_OK;
+}

@@ -155,3 +155,28 @@ def test_detailed_balance_at_long_times(oracle_mod):
             fwd, rev = kf[rr] * Pf, kb[rr] * Pb
             if max(fwd, rev) > 1e-200:
                 assert abs(np.log(fwd) - np.log(rev)) <= 1e-6, (rr, fwd, rev)
+
+
+@pytest.mark.parametrize("wl", ["h2air-1k", "hc36-256k"])
+@pytest.mark.parametrize("kappa", [0.01, 1.0])
+def test_rate_stop_stays_within_its_bound(oracle_mod, wl, kappa):
+    # the contraction-rate stop (Hairer & Wanner, Solving ODEs II, Sec. IV.8)
+    # promises that the iterate it accepts is within kappa * tolerance of the
+    # Newton limit; the iterate converged to norm <= 1 one step further stands
+    # in for that limit.  It never needs more iterations than the plain test.
+    mech, f, dt = synth.workload(wl)
+    om = oracle_mod.OracleMech(mech)
+    idx = np.linspace(0, f.n - 1, 48).astype(int)
+    fs = synth.subsample(f, idx)
+    rho, e = om.state_from_tpy(fs.T, fs.P, fs.Y)
+    h = dt / 4
+    r0, e0, a = om.advance_batch(rho, e, h, T_in=fs.T,
+                                 opts=oracle_mod.default_opts(conv_kappa=0.0, max_halvings=0))
+    r1, e1, b = om.advance_batch(rho, e, h, T_in=fs.T,
+                                 opts=oracle_mod.default_opts(conv_kappa=kappa, max_halvings=0))
+    ok = (a["status"] == 0) & (b["status"] == 0)
+    assert ok.sum() >= 12
+    tol = 1e-10 * np.abs(r0) + 1e-12 * r0.sum(0)
+    assert (np.abs(r1 - r0) / tol)[:, ok].max() <= kappa
+    assert (b["newton_iters"] <= a["newton_iters"])[ok].all()
+    assert (b["newton_iters"] < a["newton_iters"])[ok].sum() >= 4
