@@ -121,7 +121,8 @@ static int validate(const chem_mech_desc *d) {
 // Derived tables (layouts in chem_internal.h)
 struct HostTables {
     std::vector<double> thermo, tmid, sp, rxn_d, eff_c, d_c, j_c, sp_nu, exp_tab;
-    std::vector<float> rxn_df, d_cf, j_cf, sp_nuf;
+    std::vector<float> rxn_df, d_cf, spf;
+    std::vector<int2> j_pk, sp_pk;
     std::vector<int> rxn_f, eff_ptr, eff_sp, d_i0, d_i1, j_sk, j_ptr, j_d, it_ptr, sp_item_ptr, sp_r;
     int nD = 0, nD_F = 0, nD_B = 0, nD_FB = 0, nJ = 0, n_items = 0;
 };
@@ -255,20 +256,26 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         t.d_c.push_back(e.cb);
         t.d_c.push_back(e.ce);
     }
-    // species-block gather lists: -hJ_sk gathers nu_rs M_s D_rk
-    std::vector<std::vector<std::pair<int, double>>> lists((size_t)ns * ns);
+    // gather lists: J_sk gathers nu_rs M_s D_rk over the reactions r; the
+    // energy row J_ek = -sum_s e_f,s J_sk gathers -de_r D_rk with the
+    // reaction's formation-energy change de_r = sum_s nu_rs M_s e_f,s
+    std::vector<double> de(nr, 0.0);
+    for (int r = 0; r < nr; ++r)
+        for (int s = 0; s < ns; ++s) de[r] += net(r, s) * d->molar_mass[s] * ef[s];
+    std::vector<std::vector<std::pair<int, double>>> lists((size_t)(ns + 1) * ns);
     for (int j = 0; j < t.nD; ++j) {
         const int r = ents[j].r, k = ents[j].k;
         for (int s = 0; s < ns; ++s) {
             const int v = net(r, s);
             if (v != 0) lists[(size_t)s * ns + k].push_back({j, v * d->molar_mass[s]});
         }
+        if (de[r] != 0.0) lists[(size_t)ns * ns + k].push_back({j, -de[r]});
     }
-    std::vector<int> order(ns * ns);
-    for (int i = 0; i < ns * ns; ++i) order[i] = i;
+    std::vector<int> order((ns + 1) * ns);
+    for (int i = 0; i < (ns + 1) * ns; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return lists[a].size() > lists[b].size(); });
-    t.nJ = ns * ns;
+    t.nJ = (ns + 1) * ns;
     t.j_ptr.push_back(0);
     for (int idx : order) {
         const int s = idx / ns, k = idx % ns;
@@ -298,7 +305,7 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         t.sp_item_ptr[s + 1] = (int)t.it_ptr.size() - 1;
     }
     t.n_items = (int)t.it_ptr.size() - 1;
-    // 2^(j/64), from the exponential of the exact arguments in long double
+    // 2^(j/256), from the exponential of the exact arguments in long double
     t.exp_tab.resize(kExpTab);
     for (int j = 0; j < kExpTab; ++j) t.exp_tab[j] = (double)std::exp2l((long double)j / kExpTab);
     // FP32 copies for the mixed-precision Jacobian
@@ -309,11 +316,20 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         t.rxn_df[(size_t)r * kRxnDStride + 2] = (float)t.rxn_d[(size_t)r * kRxnDStride + 3];
     }
     for (double v : t.d_c) t.d_cf.push_back((float)v);
-    for (double v : t.j_c) t.j_cf.push_back((float)v);
-    for (double v : t.sp_nu) t.sp_nuf.push_back((float)v);
+    auto pack = [](int i, double c) {
+        const float f = (float)c;
+        int bits;
+        memcpy(&bits, &f, sizeof bits);
+        return make_int2(i, bits);
+    };
+    for (size_t e = 0; e < t.j_d.size(); ++e) t.j_pk.push_back(pack(t.j_d[e], t.j_c[e]));
+    for (size_t e = 0; e < t.sp_r.size(); ++e) t.sp_pk.push_back(pack(t.sp_r[e], t.sp_nu[e]));
+    for (double v : t.sp) t.spf.push_back((float)v);
     // keep every array non-empty so device pointers are valid
     auto pad_f = [](std::vector<float> &v) { if (v.empty()) v.push_back(0.0f); };
-    pad_f(t.rxn_df); pad_f(t.d_cf); pad_f(t.j_cf); pad_f(t.sp_nuf);
+    pad_f(t.rxn_df); pad_f(t.d_cf);
+    auto pad_p = [](std::vector<int2> &v) { if (v.empty()) v.push_back(make_int2(0, 0)); };
+    pad_p(t.j_pk); pad_p(t.sp_pk);
     auto pad_i = [](std::vector<int> &v) { if (v.empty()) v.push_back(0); };
     auto pad_d = [](std::vector<double> &v) { if (v.empty()) v.push_back(0.0); };
     pad_i(t.eff_sp); pad_d(t.eff_c); pad_i(t.d_i0); pad_i(t.d_i1); pad_d(t.d_c);
@@ -338,7 +354,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
                  i_jp = addv(t.j_ptr), i_jd = addv(t.j_d), i_jc = addv(t.j_c), i_itp = addv(t.it_ptr),
                  i_sip = addv(t.sp_item_ptr), i_spr = addv(t.sp_r), i_spn = addv(t.sp_nu),
                  i_ex = addv(t.exp_tab), i_rdf = addv(t.rxn_df), i_dcf = addv(t.d_cf),
-                 i_jcf = addv(t.j_cf), i_spnf = addv(t.sp_nuf);
+                 i_jpk = addv(t.j_pk), i_sppk = addv(t.sp_pk), i_spf = addv(t.spf);
     cudaError_t e = cudaMalloc(&h->dev_tables, total);
     if (e != cudaSuccess) return fail(CHEM_E_OOM, "device tables (%zu bytes): %s", total, cudaGetErrorString(e));
     h->dev_tables_bytes = total;
@@ -379,8 +395,9 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     m.exp_tab = (const double *)at(i_ex);
     m.rxn_df = (const float *)at(i_rdf);
     m.d_cf = (const float *)at(i_dcf);
-    m.j_cf = (const float *)at(i_jcf);
-    m.sp_nuf = (const float *)at(i_spnf);
+    m.j_pk = (const int2 *)at(i_jpk);
+    m.sp_pk = (const int2 *)at(i_sppk);
+    m.spf = (const float *)at(i_spf);
     return CHEM_OK;
 }
 

@@ -3,6 +3,8 @@
 
 #include <cstdint>
 
+#include <vector_types.h>
+
 #ifndef __CUDACC__
 #define __host__
 #define __device__
@@ -57,7 +59,7 @@ constexpr int kExpTab = 256;
 struct DeviceMech {
     int ns, nr;
     int nD, nD_F, nD_B, nD_FB;  // group ends: [0,F) [F,B) [B,FB) [FB,nD)
-    int nJ;                     // species-block entries (ns*ns)
+    int nJ;                     // Jacobian entries gathered: ns*ns species, ns energy-row
     int n_items;                // species-gather work items
     const double *thermo;       // [ns][2][16]
     const double *tmid;         // [ns]
@@ -70,10 +72,10 @@ struct DeviceMech {
     const int *d_i0;            // [nD]
     const int *d_i1;            // [nD]
     const double *d_c;          // [nD][3]
-    const int *j_sk;            // [nJ] s << 8 | k, longest gather list first
+    const int *j_sk;            // [nJ] s << 8 | k (s = ns: energy row), longest gather list first
     const int *j_ptr;           // [nJ+1]
     const int *j_d;             // D index of each gather term
-    const double *j_c;          // nu_rs * M_s of each gather term
+    const double *j_c;          // nu_rs M_s of each gather term; -sum_s nu_rs M_s e_f,s in the energy row
     const int *it_ptr;          // [n_items+1] ranges of the species lists
     const int *sp_item_ptr;     // [ns+1] work items of each species
     const int *sp_r;            // reactions with nu_rs != 0, per species
@@ -82,8 +84,9 @@ struct DeviceMech {
     // FP32 copies for the mixed-precision Jacobian
     const float *rxn_df;        // [nr][4] beta, Ea/R, sum nu, 0
     const float *d_cf;          // [nD][3]
-    const float *j_cf;          // gather coefficients
-    const float *sp_nuf;        // species-list coefficients
+    const int2 *j_pk;           // gather terms as {D index, FP32 coefficient bits}
+    const int2 *sp_pk;          // species lists as {reaction, FP32 nu_rs bits}
+    const float *spf;           // [ns][4] M, 1/M, R/M, e_f in FP32
 };
 
 struct StepOptions {
@@ -123,13 +126,15 @@ __host__ __device__ inline int dreg8_for(int nD, int n_items, int jt) {
 
 // Bytes of one cell slot, in this order:
 //   doubles  x, x0 (n each); c, hRT, gRT with a sentinel (ns+1 each); es, wd (ns each)
-//   JT       dTdr, w, u (ns each); for FP32 also c and hRT copies (ns+1 each)
+//   JT       dTdr (ns); w, u (ns+1 each: the species rows' T-derivative and
+//            third-body vectors, then the energy row's); for FP32 also c and
+//            hRT copies (ns+1 each)
 //   D region dreg8 * 8 bytes
 //   union    the per-reaction values Q (double) and dQdT, qtb, A1, A2 (JT),
 //            dead once the D entries exist, and the augmented matrix
 //            n x (n+1) in JT, which is written after that
 __host__ __device__ inline long long slot_small_bytes(int ns, int jt) {
-    const long long cnt = 3LL * ns + (jt == 4 ? 2LL * (ns + 1) : 0);
+    const long long cnt = 3LL * ns + 2 + (jt == 4 ? 2LL * (ns + 1) : 0);
     return (cnt * jt + 15) / 16 * 16;
 }
 __host__ __device__ inline long long slot_union_bytes(int ns, int nr, int jt) {

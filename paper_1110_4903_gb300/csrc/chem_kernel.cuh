@@ -38,7 +38,8 @@ enum SlotState : int {
 
 template <int G>
 struct Grp {
-    __device__ __forceinline__ static double sum(double v) {
+    template <typename V>
+    __device__ __forceinline__ static V sum(V v) {
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
         return v;
@@ -183,6 +184,44 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
     if (need) T_out = T;
 }
 
+// Trailing update a_ik -= l_ij a_jk of elimination step j (i > j, k > j,
+// the augmented column included), organised by columns: a lane owns a column,
+// keeps a_jk in a register and walks the rows four at a time, so four
+// independent updates are in flight and the multipliers l_ij are broadcast
+// reads.  When fewer columns than lanes remain, the rows of each column are
+// split over 2, 4, ... lanes.  Every element still receives one fused
+// multiply-add per step, in the same order of steps as the element-wise walk.
+template <int G, typename JT>
+__device__ __forceinline__ void lu_update_by_columns(JT *A, int lda, int n, int j, int sl) {
+    const int C = n - j, R = n - j - 1;
+    if (R <= 0) return;
+    int kc = sl, i0 = j + 1, i1 = n;
+    if (C < G) {
+        const int lg = C > 1 ? 32 - __clz(C - 1) : 0;   // columns rounded up to 2^lg
+        const int lgB = (__ffs(G) - 1) - lg;              // lanes per column, log2
+        const int rows = (R + (1 << lgB) - 1) >> lgB;
+        kc = sl & ((1 << lg) - 1);
+        if (kc >= C) return;
+        i0 = j + 1 + (sl >> lg) * rows;
+        i1 = min(n, i0 + rows);
+    }
+    const JT *cj = A + j;
+    for (int k = j + 1 + kc; k <= n; k += G) {
+        const JT ajk = A[j * lda + k];
+        JT *ck = A + k;
+        int i = i0;
+        for (; i + 4 <= i1; i += 4) {
+            const JT l0 = cj[i * lda], l1 = cj[(i + 1) * lda], l2 = cj[(i + 2) * lda], l3 = cj[(i + 3) * lda];
+            const JT v0 = ck[i * lda], v1 = ck[(i + 1) * lda], v2 = ck[(i + 2) * lda], v3 = ck[(i + 3) * lda];
+            ck[i * lda] = fma(-l0, ajk, v0);
+            ck[(i + 1) * lda] = fma(-l1, ajk, v1);
+            ck[(i + 2) * lda] = fma(-l2, ajk, v2);
+            ck[(i + 3) * lda] = fma(-l3, ajk, v3);
+        }
+        for (; i < i1; ++i) ck[i * lda] = fma(-cj[i * lda], ajk, ck[i * lda]);
+    }
+}
+
 template <typename JT>
 struct SlotMem {
     double *x, *x0, *c, *hRT, *gRT, *es, *wd, *Q, *part;
@@ -202,9 +241,9 @@ struct SlotMem {
         char *q = base + ((2LL * n + 3LL * (ns + 1) + 2LL * ns) * 8 + 15) / 16 * 16;
         dTdr = reinterpret_cast<JT *>(q);
         w = dTdr + ns;
-        u = w + ns;
+        u = w + ns + 1;
         if (jt == 4) {
-            cJ = u + ns;
+            cJ = u + ns + 1;
             hJ = cJ + ns + 1;
         } else {
             cJ = reinterpret_cast<JT *>(c);
@@ -304,7 +343,11 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             const JT iT = (JT)invT;
             const JT dlnkf = (JT)__ldg(rf + 1) * iT * iT + (JT)__ldg(rf) * iT;
             const JT dlnKc = (shf - (JT)__ldg(rf + 2)) * iT;
-            sm.dQdT[r] = A1v * (JT)Pf * dlnkf - A2v * (JT)Pb * (dlnkf - dlnKc);
+            // concentration products again in FP32 (a conversion costs an
+            // FP64-pipe slot, three FP32 products do not)
+            const JT PfJ = sm.cJ[a0] * sm.cJ[a1] * sm.cJ[a2];
+            const JT PbJ = sm.cJ[b0] * sm.cJ[b1] * sm.cJ[b2];
+            sm.dQdT[r] = A1v * PfJ * dlnkf - A2v * PbJ * (dlnkf - dlnKc);
         } else {
             const double sh = (sm.hRT[b0] + sm.hRT[b1] + sm.hRT[b2]) - (sm.hRT[a0] + sm.hRT[a1] + sm.hRT[a2]);
             sm.qtb[r] = tb ? (JT)q : (JT)0;
@@ -319,40 +362,69 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
 
     // 3. species sources (Eq. 26) and the rank-1 vectors of the Jacobian, as
     //    fixed-size chunks of each species' reaction list, then per species
+    //    (an item's partial sums: sum nu Q in FP64, then sum nu dQ/dT and
+    //    sum nu q_tb in the Jacobian type, packed into the next 16 bytes)
     for (int it = sl; it < m.n_items; it += G) {
         const int e0 = __ldg(m.it_ptr + it), e1 = __ldg(m.it_ptr + it + 1);
         double sq = 0.0;
         JT sdq = 0, squ = 0;
         for (int e = e0; e < e1; ++e) {
-            const int r = __ldg(m.sp_r + e);
-            const double nu = __ldg(m.sp_nu + e);
-            const JT nuj = f32 ? (JT)__ldg(m.sp_nuf + e) : (JT)nu;
+            int r;
+            double nu;
+            JT nuj;
+            if (f32) {
+                const int2 pk = __ldg(m.sp_pk + e);
+                r = pk.x;
+                nuj = (JT)__int_as_float(pk.y);
+                nu = __ldg(m.sp_nu + e);
+            } else {
+                r = __ldg(m.sp_r + e);
+                nu = __ldg(m.sp_nu + e);
+                nuj = (JT)nu;
+            }
             sq = fma(nu, sm.Q[r], sq);
             sdq += nuj * sm.dQdT[r];
             squ += nuj * sm.qtb[r];
         }
         sm.part[3 * it] = sq;
-        sm.part[3 * it + 1] = (double)sdq;
-        sm.part[3 * it + 2] = (double)squ;
+        JT *pj = reinterpret_cast<JT *>(sm.part + 3 * it + 1);
+        pj[0] = sdq;
+        pj[1] = squ;
     }
     __syncwarp();
     double wde = 0.0;
+    JT We = 0, Ue = 0;
     for (int s = sl; s < ns; s += G) {
-        double sq = 0.0, sdq = 0.0, squ = 0.0;
+        double sq = 0.0;
+        JT sdq = 0, squ = 0;
         const int i0 = __ldg(m.sp_item_ptr + s), i1 = __ldg(m.sp_item_ptr + s + 1);
         for (int it = i0; it < i1; ++it) {
             sq += sm.part[3 * it];
-            sdq += sm.part[3 * it + 1];
-            squ += sm.part[3 * it + 2];
+            const JT *pj = reinterpret_cast<const JT *>(sm.part + 3 * it + 1);
+            sdq += pj[0];
+            squ += pj[1];
         }
         const double M = __ldg(m.sp + s * kSpStride);
+        const double ef = __ldg(m.sp + s * kSpStride + 3);
+        const JT MJ = f32 ? (JT)__ldg(m.spf + s * kSpStride) : (JT)M;
+        const JT efJ = f32 ? (JT)__ldg(m.spf + s * kSpStride + 3) : (JT)ef;
         const double wds = M * sq;
         sm.wd[s] = wds;
-        sm.w[s] = (JT)(M * sdq);
-        sm.u[s] = (JT)(M * squ);
-        wde -= __ldg(m.sp + s * kSpStride + 3) * wds;
+        const JT ws = MJ * sdq, us = MJ * squ;
+        sm.w[s] = ws;
+        sm.u[s] = us;
+        wde -= ef * wds;
+        We += efJ * ws;
+        Ue += efJ * us;
     }
     wde = Grp<G>::sum(wde);
+    We = Grp<G>::sum(We);
+    Ue = Grp<G>::sum(Ue);
+    // the energy row's rank-one parts: J_ek = -sum_s e_f,s J_sk
+    if (sl == 0) {
+        sm.w[ns] = -We;
+        sm.u[ns] = -Ue;
+    }
     __syncwarp();
 
     // 4. D entries: d Q_r / d rho_k without the all-ones third-body part,
@@ -401,29 +473,28 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         sm.A[i * lda + n] = (JT)(-(sm.x[i] - sm.x0[i] - h * om));
     }
 
-    // 6. species rows of -h J (longest gather lists first, so the lanes of a
-    //    pass run lists of nearly equal length)
+    // 6. species and energy rows of -h J, density columns (longest gather
+    //    lists first, so the lanes of a pass run lists of nearly equal
+    //    length), then the temperature column
     const JT mh = (JT)(-h);
     for (int p = sl; p < m.nJ; p += G) {
         const int sk = __ldg(m.j_sk + p);
         const int s = sk >> 8, k = sk & 0xff;
-        JT J = sm.w[s] * sm.dTdr[k] + sm.u[s] * (JT)__ldg(m.sp + k * kSpStride + 1);
+        const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
+        JT J = sm.w[s] * sm.dTdr[k] + sm.u[s] * invMk;
         const int e0 = __ldg(m.j_ptr + p), e1 = __ldg(m.j_ptr + p + 1);
         if (f32) {
-            for (int e = e0; e < e1; ++e) J += (JT)__ldg(m.j_cf + e) * sm.D[__ldg(m.j_d + e)];
+            for (int e = e0; e < e1; ++e) {
+                const int2 pk = __ldg(m.j_pk + e);
+                J += (JT)__int_as_float(pk.y) * sm.D[pk.x];
+            }
         } else {
             for (int e = e0; e < e1; ++e) J += (JT)__ldg(m.j_c + e) * sm.D[__ldg(m.j_d + e)];
         }
         sm.A[s * lda + k] = mh * J;
     }
-    for (int s = sl; s < ns; s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * (JT)dTde);
-    __syncwarp();
-    // energy row: -h J_ek = -sum_s e_f,s (-h J_sk) (dense column sums)
-    for (int k = sl; k < n; k += G) {
-        JT acc = 0;
-        for (int s = 0; s < ns; ++s) acc += (JT)__ldg(m.sp + s * kSpStride + 3) * sm.A[s * lda + k];
-        sm.A[ns * lda + k] = -acc;
-    }
+    const JT dTdeJ = (JT)dTde;
+    for (int s = sl; s < n; s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * dTdeJ);
     __syncwarp();
     for (int i = sl; i < n; i += G) sm.A[i * lda + i] += (JT)1;
     if (f32) {
@@ -467,18 +538,25 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         for (int i = j + 1 + sl; i < n; i += G) sm.A[i * lda + j] *= inv;
         __syncwarp();
         if (sl == 0) sm.A[j * lda + j] = inv;
-        const int cols = n - j;
-        const int tot = (n - j - 1) * cols;
-        int e = sl;
-        int i = j + 1 + e / cols, k = j + 1 + e % cols;
-        const int di = G / cols, dk = G % cols;
-        for (; e < tot; e += G) {
-            sm.A[i * lda + k] -= sm.A[i * lda + j] * sm.A[j * lda + k];
-            i += di;
-            k += dk;
-            if (k > n) {
-                k -= cols;
-                ++i;
+        if (f32) {
+            // FP32: bound by issue and latency, not by the pipe
+            lu_update_by_columns<G, JT>(sm.A, lda, n, j, sl);
+        } else {
+            // FP64: a flat walk over the trailing elements keeps every lane of
+            // every FP64 instruction busy (a masked lane costs a full slot)
+            const int cols = n - j;
+            const int tot = (n - j - 1) * cols;
+            int e = sl;
+            int i = j + 1 + e / cols, k = j + 1 + e % cols;
+            const int di = G / cols, dk = G % cols;
+            for (; e < tot; e += G) {
+                sm.A[i * lda + k] -= sm.A[i * lda + j] * sm.A[j * lda + k];
+                i += di;
+                k += dk;
+                if (k > n) {
+                    k -= cols;
+                    ++i;
+                }
             }
         }
         __syncwarp();
