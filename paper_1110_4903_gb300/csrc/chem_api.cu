@@ -118,13 +118,67 @@ static int validate(const chem_mech_desc *d) {
     return CHEM_OK;
 }
 
+// The library orders reactions internally with the third-body reactions
+// first (stable otherwise): the rate loop's third-body branch then runs in the
+// first passes only, and the third-body progress values need ntb slots, not
+// nr.  Only internal tables see this order.
+struct ReorderedMech {
+    std::vector<double> A, beta, Ea, eff;
+    std::vector<int32_t> rs, rn, ps, pn, tb;
+    chem_mech_desc d;
+    int ntb = 0;
+};
+
+static void third_body_first(const chem_mech_desc *in, ReorderedMech &o) {
+    const int ns = in->n_species, nr = in->n_reactions;
+    std::vector<int> perm;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int r = 0; r < nr; ++r)
+            if ((in->third_body[r] != 0) == (pass == 0)) perm.push_back(r);
+    for (int r : perm) {
+        o.A.push_back(in->arr_A[r]);
+        o.beta.push_back(in->arr_beta[r]);
+        o.Ea.push_back(in->arr_Ea[r]);
+        for (int j = 0; j < 3; ++j) {
+            o.rs.push_back(in->reac_sp[r * 3 + j]);
+            o.rn.push_back(in->reac_nu[r * 3 + j]);
+            o.ps.push_back(in->prod_sp[r * 3 + j]);
+            o.pn.push_back(in->prod_nu[r * 3 + j]);
+        }
+        o.tb.push_back(in->third_body[r]);
+        if (in->third_body[r]) ++o.ntb;
+        if (in->tb_eff)
+            for (int q = 0; q < ns; ++q) o.eff.push_back(in->tb_eff[(size_t)r * ns + q]);
+    }
+    o.d = *in;
+    o.d.arr_A = o.A.data();
+    o.d.arr_beta = o.beta.data();
+    o.d.arr_Ea = o.Ea.data();
+    o.d.reac_sp = o.rs.data();
+    o.d.reac_nu = o.rn.data();
+    o.d.prod_sp = o.ps.data();
+    o.d.prod_nu = o.pn.data();
+    o.d.third_body = o.tb.data();
+    o.d.tb_eff = in->tb_eff ? o.eff.data() : nullptr;
+}
+
 // Derived tables (layouts in chem_internal.h)
 struct HostTables {
-    std::vector<double> thermo, tmid, sp, rxn_d, eff_c, d_c, j_c, sp_nu, exp_tab;
-    std::vector<float> rxn_df, d_cf, spf;
-    std::vector<int2> j_pk, sp_pk;
+    std::vector<double> thermo, tmid, tpoly, sp, rxn_d, eff_c, d_c, j_c, sp_nu, exp_tab;
+    std::vector<float> tpoly_f;
+    std::vector<float> rxn_df, d_cef, d_ef, spf;
+    std::vector<int4> d_pk;
+    std::vector<unsigned> j_w, sp_w;
     std::vector<int> rxn_f, eff_ptr, eff_sp, d_i0, d_i1, j_sk, j_ptr, j_d, it_ptr, sp_item_ptr, sp_r;
-    int nD = 0, nD_F = 0, nD_B = 0, nD_FB = 0, nJ = 0, n_items = 0;
+    std::vector<int2> j_meta;
+    std::vector<int> j_nu, sp_nui;
+    struct Layout {
+        std::vector<int2> j_meta, it_meta;
+        std::vector<unsigned> j_w, sp_w;
+        std::vector<int> j_d;
+        std::vector<double> j_c, sp_nu;
+    } lay[kLayouts];
+    int nD = 0, nD_F = 0, nD_B = 0, nD_FB = 0, nJ = 0, n_items = 0, ntb = 0;
 };
 
 static void build_tables(const chem_mech_desc *d, HostTables &t) {
@@ -159,6 +213,21 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         t.sp[s * kSpStride + 2] = kR / M;
         t.sp[s * kSpStride + 3] = ef[s];
     }
+    t.tpoly.assign((size_t)ns * 2 * kTpolyStride, 0.0);
+    t.tpoly_f.assign((size_t)ns * 2 * kTpolyFStride, 0.0f);
+    for (int s = 0; s < ns; ++s)
+        for (int rg = 0; rg < 2; ++rg) {
+            const double *a = d->nasa7 + s * 14 + rg * 7;
+            const long double RM = (long double)kR / d->molar_mass[s];
+            double *c = &t.tpoly[((size_t)s * 2 + rg) * kTpolyStride];
+            c[0] = (double)(RM * a[5] - ef[s]);
+            c[1] = (double)(RM * ((long double)a[0] - 1));
+            for (int i = 2; i <= 5; ++i) c[i] = (double)(RM * a[i - 1] / i);
+            c[6] = (double)(RM * ((long double)a[0] - 1));
+            for (int i = 1; i <= 4; ++i) c[6 + i] = (double)(RM * a[i]);
+            float *cf = &t.tpoly_f[((size_t)s * 2 + rg) * kTpolyFStride];
+            for (int i = 0; i <= 4; ++i) cf[i] = (float)c[6 + i];
+        }
     // dense stoichiometry
     std::vector<int> nuR((size_t)nr * ns, 0), nuP((size_t)nr * ns, 0);
     for (int r = 0; r < nr; ++r)
@@ -262,14 +331,16 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     std::vector<double> de(nr, 0.0);
     for (int r = 0; r < nr; ++r)
         for (int s = 0; s < ns; ++s) de[r] += net(r, s) * d->molar_mass[s] * ef[s];
-    std::vector<std::vector<std::pair<int, double>>> lists((size_t)(ns + 1) * ns);
+    struct Term { int j; double c; int nu; };
+    std::vector<std::vector<Term>> lists((size_t)(ns + 1) * ns);
     for (int j = 0; j < t.nD; ++j) {
         const int r = ents[j].r, k = ents[j].k;
         for (int s = 0; s < ns; ++s) {
             const int v = net(r, s);
-            if (v != 0) lists[(size_t)s * ns + k].push_back({j, v * d->molar_mass[s]});
+            if (v != 0) lists[(size_t)s * ns + k].push_back({j, v * d->molar_mass[s], v});
         }
-        if (de[r] != 0.0) lists[(size_t)ns * ns + k].push_back({j, -de[r]});
+        if (de[r] != 0.0) lists[(size_t)ns * ns + k].push_back({j, -de[r], 0});
+        t.d_ef.push_back((float)-de[r]);
     }
     std::vector<int> order((ns + 1) * ns);
     for (int i = 0; i < (ns + 1) * ns; ++i) order[i] = i;
@@ -280,9 +351,10 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     for (int idx : order) {
         const int s = idx / ns, k = idx % ns;
         t.j_sk.push_back((s << 8) | k);
-        for (const auto &pr : lists[idx]) {
-            t.j_d.push_back(pr.first);
-            t.j_c.push_back(pr.second);
+        for (const auto &tm : lists[idx]) {
+            t.j_d.push_back(tm.j);
+            t.j_c.push_back(tm.c);
+            t.j_nu.push_back(tm.nu);
         }
         t.j_ptr.push_back((int)t.j_d.size());
     }
@@ -296,6 +368,7 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
             if (v == 0) continue;
             t.sp_r.push_back(r);
             t.sp_nu.push_back((double)v);
+            t.sp_nui.push_back(v);
             if (++cnt == kChunk) {
                 t.it_ptr.push_back((int)t.sp_r.size());
                 cnt = 0;
@@ -315,25 +388,72 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         t.rxn_df[(size_t)r * kRxnDStride + 1] = (float)t.rxn_d[(size_t)r * kRxnDStride + 2];
         t.rxn_df[(size_t)r * kRxnDStride + 2] = (float)t.rxn_d[(size_t)r * kRxnDStride + 3];
     }
-    for (double v : t.d_c) t.d_cf.push_back((float)v);
-    auto pack = [](int i, double c) {
+    auto fbits = [](double c) {
         const float f = (float)c;
         int bits;
         memcpy(&bits, &f, sizeof bits);
-        return make_int2(i, bits);
+        return bits;
     };
-    for (size_t e = 0; e < t.j_d.size(); ++e) t.j_pk.push_back(pack(t.j_d[e], t.j_c[e]));
-    for (size_t e = 0; e < t.sp_r.size(); ++e) t.sp_pk.push_back(pack(t.sp_r[e], t.sp_nu[e]));
+    for (int j = 0; j < t.nD; ++j) {
+        t.d_pk.push_back(make_int4(t.d_i0[j], t.d_i1[j], fbits(t.d_c[3 * j]), fbits(t.d_c[3 * j + 1])));
+        t.d_cef.push_back((float)t.d_c[3 * j + 2]);
+    }
+    // a term's word: D index (or reaction) in bits 0..23, nu_rs in 24..31
+    auto word = [](int i, int nu) { return (unsigned)i | ((unsigned)(nu & 0xff) << 24); };
+    for (size_t e = 0; e < t.j_d.size(); ++e) t.j_w.push_back(word(t.j_d[e], t.j_nu[e]));
+    for (size_t e = 0; e < t.sp_r.size(); ++e) t.sp_w.push_back(word(t.sp_r[e], t.sp_nui[e]));
+    // the gather layouts for each lane count (chem_internal.h): list p on
+    // lane p % G of pass p / G, its q-th term at base(pass) + q G + lane
+    auto interleave = [](int nlists, const std::vector<int> &ptr, int G, std::vector<int2> &meta,
+                         std::vector<int> &pos, int tag_shift, const std::vector<int> *tags) {
+        int base = 0;
+        pos.assign(ptr.back(), -1);
+        for (int P0 = 0; P0 < nlists; P0 += G) {
+            const int P1 = std::min(nlists, P0 + G);
+            int maxlen = 0;
+            for (int q = P0; q < P1; ++q) maxlen = std::max(maxlen, ptr[q + 1] - ptr[q]);
+            for (int q = P0; q < P1; ++q) {
+                const int len = ptr[q + 1] - ptr[q], lane = q - P0;
+                meta.push_back(make_int2(base + lane, (tags ? (*tags)[q] : 0) | (len << tag_shift)));
+                for (int i = 0; i < len; ++i) pos[ptr[q] + i] = base + i * G + lane;
+            }
+            base += maxlen * G;
+        }
+        return base;
+    };
+    for (int li = 0; li < kLayouts; ++li) {
+        const int G = 2 << li;
+        auto &L = t.lay[li];
+        std::vector<int> pos;
+        const int nw = interleave(t.nJ, t.j_ptr, G, L.j_meta, pos, 16, &t.j_sk);
+        L.j_w.assign(std::max(nw, 1), 0u);
+        L.j_d.assign(std::max(nw, 1), 0);
+        L.j_c.assign(std::max(nw, 1), 0.0);
+        for (size_t e = 0; e < pos.size(); ++e) {
+            L.j_w[pos[e]] = t.j_w[e];
+            L.j_d[pos[e]] = t.j_d[e];
+            L.j_c[pos[e]] = t.j_c[e];
+        }
+        const int ni = interleave(t.n_items, t.it_ptr, G, L.it_meta, pos, 0, nullptr);
+        L.sp_w.assign(std::max(ni, 1), 0u);
+        L.sp_nu.assign(std::max(ni, 1), 0.0);
+        for (size_t e = 0; e < pos.size(); ++e) {
+            L.sp_w[pos[e]] = t.sp_w[e];
+            L.sp_nu[pos[e]] = t.sp_nu[e];
+        }
+        if (L.it_meta.empty()) L.it_meta.push_back(make_int2(0, 0));
+    }
     for (double v : t.sp) t.spf.push_back((float)v);
     // keep every array non-empty so device pointers are valid
     auto pad_f = [](std::vector<float> &v) { if (v.empty()) v.push_back(0.0f); };
-    pad_f(t.rxn_df); pad_f(t.d_cf);
-    auto pad_p = [](std::vector<int2> &v) { if (v.empty()) v.push_back(make_int2(0, 0)); };
-    pad_p(t.j_pk); pad_p(t.sp_pk);
+    pad_f(t.rxn_df); pad_f(t.d_cef); pad_f(t.d_ef);
+    if (t.d_pk.empty()) t.d_pk.push_back(make_int4(0, 0, 0, 0));
+    auto pad_u = [](std::vector<unsigned> &v) { if (v.empty()) v.push_back(0u); };
+    pad_u(t.j_w); pad_u(t.sp_w);
     auto pad_i = [](std::vector<int> &v) { if (v.empty()) v.push_back(0); };
     auto pad_d = [](std::vector<double> &v) { if (v.empty()) v.push_back(0.0); };
-    pad_i(t.eff_sp); pad_d(t.eff_c); pad_i(t.d_i0); pad_i(t.d_i1); pad_d(t.d_c);
-    pad_i(t.j_d); pad_d(t.j_c); pad_i(t.sp_r); pad_d(t.sp_nu); pad_i(t.rxn_f); pad_d(t.rxn_d);
+    pad_i(t.eff_sp); pad_d(t.eff_c); pad_d(t.d_c);
+    pad_i(t.j_d); pad_d(t.j_c); pad_d(t.sp_nu); pad_i(t.rxn_f); pad_d(t.rxn_d);
 }
 
 // Copies the tables into one device allocation.
@@ -348,13 +468,23 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
         return parts.size() - 1;
     };
     auto addv = [&](const auto &v) { return add(v.data(), v.size() * sizeof(v[0])); };
-    const size_t i_th = addv(t.thermo), i_tm = addv(t.tmid), i_sp = addv(t.sp), i_rd = addv(t.rxn_d),
+    const size_t i_th = addv(t.thermo), i_tm = addv(t.tmid), i_tp = addv(t.tpoly), i_tpf = addv(t.tpoly_f),
+                 i_sp = addv(t.sp), i_rd = addv(t.rxn_d),
                  i_rf = addv(t.rxn_f), i_ep = addv(t.eff_ptr), i_es = addv(t.eff_sp), i_ec = addv(t.eff_c),
-                 i_d0 = addv(t.d_i0), i_d1 = addv(t.d_i1), i_dc = addv(t.d_c), i_jsk = addv(t.j_sk),
-                 i_jp = addv(t.j_ptr), i_jd = addv(t.j_d), i_jc = addv(t.j_c), i_itp = addv(t.it_ptr),
-                 i_sip = addv(t.sp_item_ptr), i_spr = addv(t.sp_r), i_spn = addv(t.sp_nu),
-                 i_ex = addv(t.exp_tab), i_rdf = addv(t.rxn_df), i_dcf = addv(t.d_cf),
-                 i_jpk = addv(t.j_pk), i_sppk = addv(t.sp_pk), i_spf = addv(t.spf);
+                 i_dpk = addv(t.d_pk), i_dc = addv(t.d_c), i_sip = addv(t.sp_item_ptr),
+                 i_ex = addv(t.exp_tab), i_rdf = addv(t.rxn_df), i_dcef = addv(t.d_cef),
+                 i_def = addv(t.d_ef), i_spf = addv(t.spf);
+    size_t i_lay[kLayouts][7];
+    for (int li = 0; li < kLayouts; ++li) {
+        const auto &L = t.lay[li];
+        i_lay[li][0] = addv(L.j_meta);
+        i_lay[li][1] = addv(L.j_w);
+        i_lay[li][2] = addv(L.j_d);
+        i_lay[li][3] = addv(L.j_c);
+        i_lay[li][4] = addv(L.it_meta);
+        i_lay[li][5] = addv(L.sp_w);
+        i_lay[li][6] = addv(L.sp_nu);
+    }
     cudaError_t e = cudaMalloc(&h->dev_tables, total);
     if (e != cudaSuccess) return fail(CHEM_E_OOM, "device tables (%zu bytes): %s", total, cudaGetErrorString(e));
     h->dev_tables_bytes = total;
@@ -367,6 +497,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     DeviceMech &m = h->mech;
     m.ns = ns;
     m.nr = nr;
+    m.ntb = t.ntb;
     m.nD = t.nD;
     m.nD_F = t.nD_F;
     m.nD_B = t.nD_B;
@@ -375,28 +506,33 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     m.n_items = t.n_items;
     m.thermo = (const double *)at(i_th);
     m.tmid = (const double *)at(i_tm);
+    m.tpoly = (const double *)at(i_tp);
+    m.tpoly_f = (const float *)at(i_tpf);
     m.sp = (const double *)at(i_sp);
     m.rxn_d = (const double *)at(i_rd);
     m.rxn_f = (const int *)at(i_rf);
     m.eff_ptr = (const int *)at(i_ep);
     m.eff_sp = (const int *)at(i_es);
     m.eff_c = (const double *)at(i_ec);
-    m.d_i0 = (const int *)at(i_d0);
-    m.d_i1 = (const int *)at(i_d1);
+    m.d_pk = (const int4 *)at(i_dpk);
     m.d_c = (const double *)at(i_dc);
-    m.j_sk = (const int *)at(i_jsk);
-    m.j_ptr = (const int *)at(i_jp);
-    m.j_d = (const int *)at(i_jd);
-    m.j_c = (const double *)at(i_jc);
-    m.it_ptr = (const int *)at(i_itp);
+    for (int li = 0; li < kLayouts; ++li) {
+        GatherLayout &g = m.gl[li];
+        g.j_meta = (const int2 *)at(i_lay[li][0]);
+        g.j_w = (const unsigned *)at(i_lay[li][1]);
+        g.j_d = (const int *)at(i_lay[li][2]);
+        g.j_c = (const double *)at(i_lay[li][3]);
+        g.it_meta = (const int2 *)at(i_lay[li][4]);
+        g.sp_w = (const unsigned *)at(i_lay[li][5]);
+        g.sp_nu = (const double *)at(i_lay[li][6]);
+    }
     m.sp_item_ptr = (const int *)at(i_sip);
-    m.sp_r = (const int *)at(i_spr);
-    m.sp_nu = (const double *)at(i_spn);
+
     m.exp_tab = (const double *)at(i_ex);
     m.rxn_df = (const float *)at(i_rdf);
-    m.d_cf = (const float *)at(i_dcf);
-    m.j_pk = (const int2 *)at(i_jpk);
-    m.sp_pk = (const int2 *)at(i_sppk);
+    m.d_cef = (const float *)at(i_dcef);
+    m.d_ef = (const float *)at(i_def);
+
     m.spf = (const float *)at(i_spf);
     return CHEM_OK;
 }
@@ -408,7 +544,7 @@ int configure(Handle *h, int prec, int G, int wpb_req, LaunchCfg &cfg) {
     const void *fn = prec == CHEM_MIXED ? be_kernel_mixed(G) : be_kernel_fp64(G);
     if (!fn) return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d not available", G);
     const int S = 32 / G;
-    const long long sb = slot_bytes_for(h->mech.ns, h->mech.nr, h->mech.nD, h->mech.n_items, prec == CHEM_MIXED ? 4 : 8);
+    const long long sb = slot_bytes_for(h->mech, prec == CHEM_MIXED ? 4 : 8);
     int best_warps = 0;
     LaunchCfg best{};
     // the attribute is per function and shared by every handle: allow the
@@ -416,7 +552,7 @@ int configure(Handle *h, int prec, int G, int wpb_req, LaunchCfg &cfg) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)h->max_smem_optin);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    for (int wpb : {8, 4, 2, 1}) {
+    for (int wpb = 8; wpb >= 1; --wpb) {
         if (wpb_req && wpb != wpb_req) continue;
         const long long smem = kBlockHeaderBytes + (long long)wpb * S * sb;
         if (smem > h->max_smem_optin) continue;
@@ -633,8 +769,11 @@ int chem_create(const chem_mech_desc *mech, const chem_options *opts, chem_handl
     if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDeviceProperties"); }
     h->num_sms = prop.multiProcessorCount;
     h->max_smem_optin = (long long)prop.sharedMemPerBlockOptin;
+    ReorderedMech rm;
+    third_body_first(mech, rm);
     HostTables t;
-    build_tables(mech, t);
+    build_tables(&rm.d, t);
+    t.ntb = rm.ntb;
     h->ef_host.resize(h->ns);
     for (int s = 0; s < h->ns; ++s) h->ef_host[s] = t.sp[s * kSpStride + 3];
     rc = upload(t, h->ns, h->nr, h);

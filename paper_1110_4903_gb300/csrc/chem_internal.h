@@ -29,6 +29,15 @@ constexpr double kTtol = 1e-13;        // |dT| <= kTtol * T ends the recovery
 //   13    a7
 constexpr int kThermoStride = 16;
 
+// Energy polynomials per species and range (12 doubles), the NASA-7 forms
+// multiplied out with R/M and shifted by the formation energy:
+//   0..5  e_s(T) - e_f,s = c0 + c1 T + ... + c5 T^5  (c0 = R/M a6 - e_f,
+//         c1 = R/M (a1 - 1), c_i = R/M a_i / i for i = 2..5)
+//   6..10 c_v,s(T) = R/M (cp/R - 1) = d0 + d1 T + ... + d4 T^4
+// and an FP32 copy of d0..d4 (8 floats per row).
+constexpr int kTpolyStride = 12;
+constexpr int kTpolyFStride = 8;
+
 // Species table row (4 doubles): M, 1/M, R/M, e_f = e_s(T_ref).
 constexpr int kSpStride = 4;
 
@@ -52,40 +61,64 @@ constexpr int kExpTab = 256;
 // progress rate Q_r depends on, holding dQ_r/drho_k without the all-ones
 // third-body part.  They are sorted into four groups so each group is one
 // uniform loop: reactant-only, product-only, both sides, efficiency-only.
-//   d_i0 = r | k << 16
-//   d_i1 = fa | fb << 8 | ba << 16 | bb << 24  (the remaining factors of
-//          d(prod c)/dc_k on each side, sentinel ns if none)
-//   d_c  = {nu'_rk / M_k, nu''_rk / M_k, (alpha_rk - 1) / M_k}
+//   d_pk = {r | k << 16,
+//           fa | fb << 8 | ba << 16 | bb << 24  (the remaining factors of
+//                d(prod c)/dc_k on each side, sentinel ns if none),
+//           FP32 bits of nu'_rk / M_k, FP32 bits of nu''_rk / M_k}
+//   d_c  = {nu'_rk / M_k, nu''_rk / M_k, (alpha_rk - 1) / M_k} (FP64)
+//   d_cef = (alpha_rk - 1) / M_k (FP32)
+// Gather lists laid out for G lanes per cell.  List p (a Jacobian entry, or
+// an item of a species list) runs in pass p / G on lane p % G; its q-th term
+// sits at word base + q G + lane, where base is the pass's first word, so the
+// lanes of a pass read their q-th terms from consecutive words (one cache
+// line per warp load instead of one per lane).
+//   j_meta[p]  = {first word of entry p, k | s << 8 | terms << 16}
+//   j_w        = D index | nu_rs << 24 (species rows), D index (energy row)
+//   j_d, j_c   = D index and FP64 coefficient nu_rs M_s (or -de_r)
+//   it_meta[i] = {first word of item i, entries}
+//   sp_w       = r | nu_rs << 24;  sp_nu = nu_rs (FP64)
+struct GatherLayout {
+    const int2 *j_meta;
+    const unsigned *j_w;
+    const int *j_d;
+    const double *j_c;
+    const int2 *it_meta;
+    const unsigned *sp_w;
+    const double *sp_nu;
+};
+constexpr int kLayouts = 5;   // G = 2, 4, 8, 16, 32
+__host__ __device__ constexpr int layout_index(int G) {
+    return G == 2 ? 0 : G == 4 ? 1 : G == 8 ? 2 : G == 16 ? 3 : 4;
+}
+
 struct DeviceMech {
     int ns, nr;
+    int ntb;                    // third-body reactions: the first ntb (internal order)
     int nD, nD_F, nD_B, nD_FB;  // group ends: [0,F) [F,B) [B,FB) [FB,nD)
     int nJ;                     // Jacobian entries gathered: ns*ns species, ns energy-row
     int n_items;                // species-gather work items
     const double *thermo;       // [ns][2][16]
-    const double *tmid;         // [ns]
+    const double *tmid;         // [ns] (positive: compared as integers)
+    const double *tpoly;        // [ns][2][12] energy and heat-capacity polynomials
+    const float *tpoly_f;       // [ns][2][8] heat-capacity polynomial in FP32
     const double *sp;           // [ns][4]
     const double *rxn_d;        // [nr][4]
     const int *rxn_f;           // [nr][2]
     const int *eff_ptr;         // [nr+1] CSR of efficiency corrections of +M reactions
     const int *eff_sp;          //        species
     const double *eff_c;        //        alpha - 1
-    const int *d_i0;            // [nD]
-    const int *d_i1;            // [nD]
+    const int4 *d_pk;           // [nD]
     const double *d_c;          // [nD][3]
-    const int *j_sk;            // [nJ] s << 8 | k (s = ns: energy row), longest gather list first
-    const int *j_ptr;           // [nJ+1]
-    const int *j_d;             // D index of each gather term
-    const double *j_c;          // nu_rs M_s of each gather term; -sum_s nu_rs M_s e_f,s in the energy row
-    const int *it_ptr;          // [n_items+1] ranges of the species lists
+    // Jacobian entries (s = ns: energy row), longest gather list first, and
+    // the species lists (reactions with nu_rs != 0) cut into items of at
+    // most kChunk entries; per-G layouts above
+    GatherLayout gl[kLayouts];
     const int *sp_item_ptr;     // [ns+1] work items of each species
-    const int *sp_r;            // reactions with nu_rs != 0, per species
-    const double *sp_nu;        // nu_rs
     const double *exp_tab;      // [kExpTab] 2^(j/kExpTab)
     // FP32 copies for the mixed-precision Jacobian
     const float *rxn_df;        // [nr][4] beta, Ea/R, sum nu, 0
-    const float *d_cf;          // [nD][3]
-    const int2 *j_pk;           // gather terms as {D index, FP32 coefficient bits}
-    const int2 *sp_pk;          // species lists as {reaction, FP32 nu_rs bits}
+    const float *d_cef;         // [nD] efficiency coefficient in FP32
+    const float *d_ef;          // [nD] energy-row coefficient of the D entry's reaction
     const float *spf;           // [ns][4] M, 1/M, R/M, e_f in FP32
 };
 
@@ -130,23 +163,24 @@ __host__ __device__ inline int dreg8_for(int nD, int n_items, int jt) {
 //            third-body vectors, then the energy row's); for FP32 also c and
 //            hRT copies (ns+1 each)
 //   D region dreg8 * 8 bytes
-//   union    the per-reaction values Q (double) and dQdT, qtb, A1, A2 (JT),
-//            dead once the D entries exist, and the augmented matrix
-//            n x (n+1) in JT, which is written after that
+//   union    the per-reaction values Q (double), dQdT, A1, A2 (JT) and the
+//            third-body progress qtb (JT, ntb entries), dead once the D
+//            entries exist, and the augmented matrix n x (n+1) in JT, which
+//            is written after that
 __host__ __device__ inline long long slot_small_bytes(int ns, int jt) {
     const long long cnt = 3LL * ns + 2 + (jt == 4 ? 2LL * (ns + 1) : 0);
     return (cnt * jt + 15) / 16 * 16;
 }
-__host__ __device__ inline long long slot_union_bytes(int ns, int nr, int jt) {
+__host__ __device__ inline long long slot_union_bytes(int ns, int nr, int ntb, int jt) {
     const int n = ns + 1;
-    const long long a = (long long)nr * 8 + 4LL * nr * jt, b = (long long)n * (n + 1) * jt;
+    const long long a = (long long)nr * 8 + 3LL * nr * jt + (long long)ntb * jt, b = (long long)n * (n + 1) * jt;
     return ((a > b ? a : b) + 15) / 16 * 16;
 }
-__host__ __device__ inline long long slot_bytes_for(int ns, int nr, int nD, int n_items, int jt) {
-    const int n = ns + 1;
+__host__ __device__ inline long long slot_bytes_for(const DeviceMech &m, int jt) {
+    const int ns = m.ns, n = ns + 1;
     const long long dbl = (2LL * n + 3LL * (ns + 1) + 2LL * ns) * 8;
-    const long long dreg = ((long long)dreg8_for(nD, n_items, jt) * 8 + 15) / 16 * 16;
-    return (dbl + 15) / 16 * 16 + slot_small_bytes(ns, jt) + dreg + slot_union_bytes(ns, nr, jt);
+    const long long dreg = ((long long)dreg8_for(m.nD, m.n_items, jt) * 8 + 15) / 16 * 16;
+    return (dbl + 15) / 16 * 16 + slot_small_bytes(ns, jt) + dreg + slot_union_bytes(ns, m.nr, m.ntb, jt);
 }
 
 }  // namespace chem

@@ -44,7 +44,8 @@ struct Grp {
         for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
         return v;
     }
-    __device__ __forceinline__ static double max(double v) {
+    template <typename V>
+    __device__ __forceinline__ static V max(V v) {
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
         return v;
@@ -67,6 +68,53 @@ struct Grp {
         }
     }
 };
+
+// Conversions between FP64 and FP32 on the integer pipe: on this part a
+// conversion instruction occupies the FP64 pipe as long as a DFMA does.
+// FP64 -> FP32 rounds toward zero; magnitudes below the smallest normal
+// float give a signed zero, above the largest an infinity; NaN stays NaN.
+__device__ __forceinline__ float d2f_rz(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const unsigned man = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    unsigned f = sign | ((unsigned)e << 23) | man;
+    if (e <= 0) f = sign;
+    if (e >= 255) f = sign | 0x7f800000u | ((e == 1151 && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
+    return __uint_as_float(f);
+}
+// FP32 -> FP64, exact for normal floats and infinities (NaN stays NaN,
+// subnormal floats give a signed zero).
+__device__ __forceinline__ double f2d_alu(float v) {
+    const unsigned u = __float_as_uint(v);
+    const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+    unsigned hi = sign | ((e + 896u) << 20) | (man >> 3);
+    unsigned lo = man << 29;
+    if (e == 0) {
+        hi = sign;
+        lo = 0u;
+    }
+    if (e == 255u) hi = sign | 0x7ff00000u | (man >> 3);
+    return __hiloint2double((int)hi, (int)lo);
+}
+template <typename JT> __device__ __forceinline__ JT to_jt(double v);
+template <> __device__ __forceinline__ double to_jt<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_jt<float>(double v) { return d2f_rz(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return f2d_alu(v); }
+
+// Order of doubles by their bit patterns (integer pipe): exact for a >= 0
+// against b > 0; a negative a counts as smaller, a NaN a as larger.
+__device__ __forceinline__ bool bits_gt(double a, double b) {
+    return __double_as_longlong(a) > __double_as_longlong(b);
+}
+__device__ __forceinline__ bool bits_lt(double a, double b) {
+    return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ bool finite_bits(double v) {
+    return ((unsigned)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffu) != 0x7ffu;
+}
 
 // |v| as an ordered integer key (NaN maps to 0 so it is never the pivot).
 __device__ __forceinline__ unsigned long long abs_key(double v) {
@@ -95,6 +143,16 @@ __device__ __forceinline__ double frcp(double a) {
 }
 __device__ __forceinline__ float frcp(float a) { return __frcp_rn(a); }
 
+// The library exp for the arguments the table path does not take; kept out
+// of line so its code is not repeated at every call site.
+static __device__ __noinline__ double exp_outside(double x) { return exp(x); }
+
+// A small signed integer (|v| < 2^22) as a float without a conversion
+// instruction: add it to the bit pattern of 1.5 * 2^23, whose ulp is 1.
+__device__ __forceinline__ float small_int_to_float(int v) {
+    return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+
 // exp by the table-driven reduction of P. T. P. Tang, ACM TOMS 15(2), 1989:
 // x = (256 k + j) ln2/256 + r with |r| <= ln2/512, exp(x) = 2^k 2^(j/256) e^r,
 // 2^(j/256) from a 256-entry table and e^r - 1 by its degree-4 Taylor
@@ -103,7 +161,7 @@ __device__ __forceinline__ float frcp(float a) { return __frcp_rn(a); }
 // no FP64 compare) fall back to the library exp.
 __device__ __forceinline__ double fexp(double x, const double *tab) {
     const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
-    if (((hi >> 20) & 0x7ffu) > 0x407u) return exp(x);
+    if (((hi >> 20) & 0x7ffu) > 0x407u) return exp_outside(x);
     const double kShift = 6755399441055744.0;               // 1.5 * 2^52
     const double t = fma(x, 369.3299304675746, kShift);     // x * 256/ln2, rounded
     const int n = (int)(unsigned)__double_as_longlong(t);
@@ -120,58 +178,75 @@ __device__ __forceinline__ double fexp(double x, const double *tab) {
     return __longlong_as_double(__double_as_longlong(y) + (k << 52));
 }
 
-// NASA-7 evaluations from a 16-double thermo row (layout in chem_internal.h)
-__device__ __forceinline__ void nasa_cp_h(const double *th, double T, double invT, double &cpR,
-                                          double &hRT) {
-    cpR = th[0] + T * (th[1] + T * (th[2] + T * (th[3] + T * th[4])));
-    hRT = th[0] + T * (th[5] + T * (th[6] + T * (th[7] + T * th[8]))) + th[9] * invT;
-}
+// NASA-7 entropy from a 16-double thermo row (layout in chem_internal.h)
 __device__ __forceinline__ double nasa_s(const double *th, double T, double lnT) {
     return th[0] * lnT + T * (th[1] + T * (th[10] + T * (th[11] + T * th[12]))) + th[13];
 }
-__device__ __forceinline__ const double *thermo_row(const DeviceMech &m, int s, double T) {
-    return m.thermo + (size_t)(s * 2 + (T > __ldg(m.tmid + s) ? 1 : 0)) * kThermoStride;
+// range of species s at T (T > T_mid: high range), as a row index
+__device__ __forceinline__ int thermo_range_row(const DeviceMech &m, int s, long long Tbits) {
+    return s * 2 + (Tbits > __ldg(reinterpret_cast<const long long *>(m.tmid) + s) ? 1 : 0);
 }
 
 // Temperature recovery from (rho_s, e) for every slot whose `need` is set:
 // Newton on sum_s rho_s e_s^sens(T) = e, safeguarded by bisection on
 // [kTlo, kThi], stop at |dT| <= kTtol T (Eq. 3 with the kinetic energy left to
 // the flux stage).  Uniform across the warp.
-template <int G>
+//   The energies come from the multiplied-out polynomials (five DFMA per
+//   species, no 1/T); with F32 the derivative sum c_v is formed in FP32, which
+//   changes the Newton steps by a relative 1e-7 and not the root.
+template <int G, bool F32>
 __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, int sl, bool need,
                                           double guess, double &T_out, bool &ok) {
     const int ns = m.ns;
     double lo = kTlo, hi = kThi, T = guess;
-    if (!(T > lo && T < hi)) T = 1500.0;
+    if (!(bits_gt(T, lo) && bits_lt(T, hi))) T = 1500.0;
     bool done = !need;
     ok = false;
     const double e = x[ns];
     for (int it = 1; it <= kTmaxIter; ++it) {
         if (!__any_sync(kFull, !done)) break;
-        const double invT = frcp(T);
+        const long long Tb = __double_as_longlong(T);
+        const float Tf = F32 ? d2f_rz(T) : 0.f;
         double f = 0.0, fp = 0.0;
+        float fpf = 0.f;
         for (int s = sl; s < ns; s += G) {
-            const double *th = thermo_row(m, s, T);
-            double cpR, hRT;
-            nasa_cp_h(th, T, invT, cpR, hRT);
-            const double RM = __ldg(m.sp + s * kSpStride + 2);
-            const double ef = __ldg(m.sp + s * kSpStride + 3);
-            f += x[s] * (RM * T * (hRT - 1.0) - ef);
-            fp += x[s] * (RM * (cpR - 1.0));
+            const int row = thermo_range_row(m, s, Tb);
+            const double *c = m.tpoly + (size_t)row * kTpolyStride;
+            const double es = fma(fma(fma(fma(fma(__ldg(c + 5), T, __ldg(c + 4)), T, __ldg(c + 3)), T, __ldg(c + 2)), T,
+                                      __ldg(c + 1)), T, __ldg(c));
+            f = fma(x[s], es, f);
+            if (F32) {
+                const float *d = m.tpoly_f + (size_t)row * kTpolyFStride;
+                const float cv = fmaf(fmaf(fmaf(fmaf(__ldg(d + 4), Tf, __ldg(d + 3)), Tf, __ldg(d + 2)), Tf, __ldg(d + 1)),
+                                      Tf, __ldg(d));
+                fpf = fmaf(d2f_rz(x[s]), cv, fpf);
+            } else {
+                const double cv = fma(fma(fma(fma(__ldg(c + 10), T, __ldg(c + 9)), T, __ldg(c + 8)), T, __ldg(c + 7)), T,
+                                      __ldg(c + 6));
+                fp = fma(x[s], cv, fp);
+            }
         }
         f = Grp<G>::sum(f) - e;
-        fp = Grp<G>::sum(fp);
+        double rfp;
+        if (F32) {
+            fpf = Grp<G>::sum(fpf);
+            rfp = f2d_alu(__frcp_rn(fpf));
+        } else {
+            fp = Grp<G>::sum(fp);
+            rfp = frcp(fp);
+        }
         if (!done) {
-            if (f == 0.0) {
+            const long long fb = __double_as_longlong(f);
+            if ((fb << 1) == 0) {
                 done = true;
                 ok = true;
             } else {
-                if (f > 0.0)
+                if (fb > 0)
                     hi = T;
                 else
                     lo = T;
-                double Tn = T - f * frcp(fp);
-                if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+                double Tn = T - f * rfp;
+                if (!(bits_gt(Tn, lo) && bits_lt(Tn, hi))) Tn = 0.5 * (lo + hi);
                 const double dT = Tn - T;
                 T = Tn;
                 if (fabs(dT) <= kTtol * T) {
@@ -256,9 +331,9 @@ struct SlotMem {
         // union: per-reaction rates, then (after the D entries) the matrix
         Q = reinterpret_cast<double *>(q);
         dQdT = reinterpret_cast<JT *>(Q + nr);
-        qtb = dQdT + nr;
-        A1 = qtb + nr;
+        A1 = dQdT + nr;
         A2 = A1 + nr;
+        qtb = A2 + nr;
         A = reinterpret_cast<JT *>(q);
     }
 };
@@ -276,26 +351,39 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     const double lnT = log(T);
     const double lnPaRT = log(kPa / kR) - lnT;
 
-    // 1. concentrations and thermodynamics (species)
+    // 1. concentrations and thermodynamics (species); the heat capacity only
+    //    feeds dT/drho, dT/de and the next temperature guess, so the FP32
+    //    path forms it in FP32
+    const long long Tb = __double_as_longlong(T);
+    const float Tf = f32 ? d2f_rz(T) : 0.f;
     double ctot = 0.0, rhocv = 0.0;
+    float rhocvf = 0.f;
     for (int s = sl; s < ns; s += G) {
         const double *spr = m.sp + s * kSpStride;
         const double xs = sm.x[s];
         const double ci = xs * __ldg(spr + 1);
         sm.c[s] = ci;
         ctot += ci;
-        const double *th = thermo_row(m, s, T);
-        double cpR, hRT;
-        nasa_cp_h(th, T, invT, cpR, hRT);
+        const int row = thermo_range_row(m, s, Tb);
+        const double *th = m.thermo + (size_t)row * kThermoStride;
+        const double hRT = th[0] + T * (th[5] + T * (th[6] + T * (th[7] + T * th[8]))) + th[9] * invT;
         const double sR = nasa_s(th, T, lnT);
         const double RM = __ldg(spr + 2);
         sm.hRT[s] = hRT;
         sm.gRT[s] = hRT - sR;
         sm.es[s] = RM * T * (hRT - 1.0) - __ldg(spr + 3);
-        rhocv += xs * (RM * (cpR - 1.0));
         if (f32) {
-            sm.cJ[s] = (JT)ci;
-            sm.hJ[s] = (JT)hRT;
+            const float *d = m.tpoly_f + (size_t)row * kTpolyFStride;
+            const float cv = fmaf(fmaf(fmaf(fmaf(__ldg(d + 4), Tf, __ldg(d + 3)), Tf, __ldg(d + 2)), Tf, __ldg(d + 1)),
+                                  Tf, __ldg(d));
+            rhocvf = fmaf(d2f_rz(xs), cv, rhocvf);
+            sm.cJ[s] = to_jt<JT>(ci);
+            sm.hJ[s] = to_jt<JT>(hRT);
+        } else {
+            const double *c = m.tpoly + (size_t)row * kTpolyStride;
+            const double cv = fma(fma(fma(fma(__ldg(c + 10), T, __ldg(c + 9)), T, __ldg(c + 8)), T, __ldg(c + 7)), T,
+                                  __ldg(c + 6));
+            rhocv = fma(xs, cv, rhocv);
         }
     }
     if (f32 && sl == 0) {
@@ -303,13 +391,23 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         sm.hJ[ns] = (JT)0;
     }
     ctot = Grp<G>::sum(ctot);
-    rhocv = Grp<G>::sum(rhocv);
-    const double dTde = frcp(rhocv);
-    for (int s = sl; s < ns; s += G) sm.dTdr[s] = (JT)(-sm.es[s] * dTde);
+    double dTde;
+    float dTdef = 0.f;
+    if (f32) {
+        rhocvf = Grp<G>::sum(rhocvf);
+        dTdef = __frcp_rn(rhocvf);
+        dTde = f2d_alu(dTdef);
+        for (int s = sl; s < ns; s += G) sm.dTdr[s] = (JT)(-d2f_rz(sm.es[s]) * dTdef);
+    } else {
+        rhocv = Grp<G>::sum(rhocv);
+        dTde = frcp(rhocv);
+        for (int s = sl; s < ns; s += G) sm.dTdr[s] = (JT)(-sm.es[s] * dTde);
+    }
     __syncwarp();
 
     // 2. rates per reaction: Eq. 23 forward rate, Eq. 24 equilibrium
     //    constant, Eq. 25 progress rate, and their temperature derivatives
+    const JT iT = to_jt<JT>(invT);
     for (int r = sl; r < nr; r += G) {
         const double *rd = m.rxn_d + (size_t)r * kRxnDStride;
         const double lnA = __ldg(rd + 0), beta = __ldg(rd + 1), EaR = __ldg(rd + 2), dnu = __ldg(rd + 3);
@@ -335,12 +433,11 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         if (f32) {
             // Jacobian-only quantities in FP32 from FP32 copies
             const float* rf = m.rxn_df + (size_t)r * kRxnDStride;
-            const JT A1v = (JT)(CM * kf), A2v = (JT)(CM * kb);
+            const JT A1v = to_jt<JT>(CM * kf), A2v = to_jt<JT>(CM * kb);
             sm.A1[r] = A1v;
             sm.A2[r] = A2v;
-            sm.qtb[r] = tb ? (JT)q : (JT)0;
+            if (r < m.ntb) sm.qtb[r] = to_jt<JT>(q);
             const JT shf = (sm.hJ[b0] + sm.hJ[b1] + sm.hJ[b2]) - (sm.hJ[a0] + sm.hJ[a1] + sm.hJ[a2]);
-            const JT iT = (JT)invT;
             const JT dlnkf = (JT)__ldg(rf + 1) * iT * iT + (JT)__ldg(rf) * iT;
             const JT dlnKc = (shf - (JT)__ldg(rf + 2)) * iT;
             // concentration products again in FP32 (a conversion costs an
@@ -350,7 +447,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             sm.dQdT[r] = A1v * PfJ * dlnkf - A2v * PbJ * (dlnkf - dlnKc);
         } else {
             const double sh = (sm.hRT[b0] + sm.hRT[b1] + sm.hRT[b2]) - (sm.hRT[a0] + sm.hRT[a1] + sm.hRT[a2]);
-            sm.qtb[r] = tb ? (JT)q : (JT)0;
+            if (r < m.ntb) sm.qtb[r] = (JT)q;
             sm.A1[r] = (JT)(CM * kf);
             sm.A2[r] = (JT)(CM * kb);
             const double dlnkf = fma(EaR * invT, invT, beta * invT);
@@ -364,27 +461,23 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     //    fixed-size chunks of each species' reaction list, then per species
     //    (an item's partial sums: sum nu Q in FP64, then sum nu dQ/dT and
     //    sum nu q_tb in the Jacobian type, packed into the next 16 bytes)
+    const GatherLayout &gl = m.gl[layout_index(G)];
     for (int it = sl; it < m.n_items; it += G) {
-        const int e0 = __ldg(m.it_ptr + it), e1 = __ldg(m.it_ptr + it + 1);
+        const int2 im = __ldg(gl.it_meta + it);
         double sq = 0.0;
         JT sdq = 0, squ = 0;
-        for (int e = e0; e < e1; ++e) {
-            int r;
-            double nu;
-            JT nuj;
-            if (f32) {
-                const int2 pk = __ldg(m.sp_pk + e);
-                r = pk.x;
-                nuj = (JT)__int_as_float(pk.y);
-                nu = __ldg(m.sp_nu + e);
-            } else {
-                r = __ldg(m.sp_r + e);
-                nu = __ldg(m.sp_nu + e);
-                nuj = (JT)nu;
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            if (q < im.y) {
+                const int e = im.x + q * G;
+                const unsigned wv = __ldg(gl.sp_w + e);
+                const int r = (int)(wv & 0xffffffu);
+                const double nu = __ldg(gl.sp_nu + e);
+                const JT nuj = f32 ? (JT)small_int_to_float((int)wv >> 24) : (JT)nu;
+                sq = fma(nu, sm.Q[r], sq);
+                sdq += nuj * sm.dQdT[r];
+                if (r < m.ntb) squ += nuj * sm.qtb[r];
             }
-            sq = fma(nu, sm.Q[r], sq);
-            sdq += nuj * sm.dQdT[r];
-            squ += nuj * sm.qtb[r];
         }
         sm.part[3 * it] = sq;
         JT *pj = reinterpret_cast<JT *>(sm.part + 3 * it + 1);
@@ -428,26 +521,41 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     __syncwarp();
 
     // 4. D entries: d Q_r / d rho_k without the all-ones third-body part,
-    //    grouped so that each group is one uniform loop body
+    //    grouped so that each group is one uniform loop body (FP32: one
+    //    branch-free body that selects the sides by group, two entries per
+    //    trip so their loads overlap)
+    if (f32) {
+        const JT *__restrict__ A1v = sm.A1;
+        const JT *__restrict__ A2v = sm.A2;
+        const JT *__restrict__ cJv = sm.cJ;
+        const JT *__restrict__ qv = sm.qtb;
+        JT *__restrict__ Dw = sm.D;
+        auto dval = [&](int j) -> JT {
+            const int4 pk = __ldg(m.d_pk + j);
+            const int r = pk.x & 0xffff, i1 = pk.y;
+            const JT fwd = (JT)__int_as_float(pk.z) * A1v[r] * (cJv[i1 & 0xff] * cJv[(i1 >> 8) & 0xff]);
+            const JT bwd = (JT)__int_as_float(pk.w) * A2v[r] * (cJv[(i1 >> 16) & 0xff] * cJv[(i1 >> 24) & 0xff]);
+            const bool hasf = j < m.nD_F || (j >= m.nD_B && j < m.nD_FB);
+            const bool hasb = j >= m.nD_F && j < m.nD_FB;
+            JT d = (hasf ? fwd : (JT)0) - (hasb ? bwd : (JT)0);
+            if (r < m.ntb) d = fma((JT)__ldg(m.d_cef + j), qv[r], d);
+            return d;
+        };
+        int j = sl;
+        for (; j + G < m.nD; j += 2 * G) {
+            const JT d0 = dval(j), d1 = dval(j + G);
+            Dw[j] = d0;
+            Dw[j + G] = d1;
+        }
+        if (j < m.nD) Dw[j] = dval(j);
+    } else
     for (int j = sl; j < m.nD; j += G) {
-        const int i0 = __ldg(m.d_i0 + j), i1 = __ldg(m.d_i1 + j);
+        const int2 pk = __ldg(reinterpret_cast<const int2 *>(m.d_pk + j));
+        const int i0 = pk.x, i1 = pk.y;
         const int r = i0 & 0xffff;
         const int fa = i1 & 0xff, fb = (i1 >> 8) & 0xff, ba = (i1 >> 16) & 0xff, bb = (i1 >> 24) & 0xff;
         JT d;
-        if (f32) {
-            const float *dc = m.d_cf + 3 * (size_t)j;
-            if (j < m.nD_F) {
-                d = (JT)__ldg(dc) * sm.A1[r] * (sm.cJ[fa] * sm.cJ[fb]);
-            } else if (j < m.nD_B) {
-                d = -(JT)__ldg(dc + 1) * sm.A2[r] * (sm.cJ[ba] * sm.cJ[bb]);
-            } else if (j < m.nD_FB) {
-                d = (JT)__ldg(dc) * sm.A1[r] * (sm.cJ[fa] * sm.cJ[fb]) -
-                    (JT)__ldg(dc + 1) * sm.A2[r] * (sm.cJ[ba] * sm.cJ[bb]);
-            } else {
-                d = 0;
-            }
-            d += (JT)__ldg(dc + 2) * sm.qtb[r];
-        } else {
+        {
             const double *dc = m.d_c + 3 * (size_t)j;
             double dd;
             if (j < m.nD_F) {
@@ -460,7 +568,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             } else {
                 dd = 0.0;
             }
-            d = (JT)fma(__ldg(dc + 2), (double)sm.qtb[r], dd);
+            d = r < m.ntb ? (JT)fma(__ldg(dc + 2), (double)sm.qtb[r], dd) : (JT)dd;
         }
         sm.D[j] = d;
     }
@@ -470,30 +578,60 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     // 5. right-hand side -F = -(x - x0 - h Omega(x))
     for (int i = sl; i < n; i += G) {
         const double om = i < ns ? sm.wd[i] : wde;
-        sm.A[i * lda + n] = (JT)(-(sm.x[i] - sm.x0[i] - h * om));
+        sm.A[i * lda + n] = to_jt<JT>(-(sm.x[i] - sm.x0[i] - h * om));
     }
 
     // 6. species and energy rows of -h J, density columns (longest gather
     //    lists first, so the lanes of a pass run lists of nearly equal
     //    length), then the temperature column
-    const JT mh = (JT)(-h);
+    //    (four terms in flight per trip, two accumulators)
+    const JT mh = to_jt<JT>(-h);
+    const JT *__restrict__ Dv = sm.D;
     for (int p = sl; p < m.nJ; p += G) {
-        const int sk = __ldg(m.j_sk + p);
-        const int s = sk >> 8, k = sk & 0xff;
+        const int2 meta = __ldg(gl.j_meta + p);
+        const int len = meta.y >> 16;
+        const int s = (meta.y >> 8) & 0xff, k = meta.y & 0xff;
         const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
         JT J = sm.w[s] * sm.dTdr[k] + sm.u[s] * invMk;
-        const int e0 = __ldg(m.j_ptr + p), e1 = __ldg(m.j_ptr + p + 1);
+        JT a0 = 0, a1 = 0;
+        int e = meta.x, q = 0;
         if (f32) {
-            for (int e = e0; e < e1; ++e) {
-                const int2 pk = __ldg(m.j_pk + e);
-                J += (JT)__int_as_float(pk.y) * sm.D[pk.x];
+            // species row: M_s sum nu_rs D_rk; energy row: sum (-de_r) D_rk
+            const bool erow = s == ns;
+            auto coef = [&](unsigned wv) -> JT {
+                return erow ? (JT)__ldg(m.d_ef + (wv & 0xffffffu)) : (JT)small_int_to_float((int)wv >> 24);
+            };
+            for (; q + 4 <= len; q += 4, e += 4 * G) {
+                const unsigned w0 = __ldg(gl.j_w + e), w1 = __ldg(gl.j_w + e + G), w2 = __ldg(gl.j_w + e + 2 * G),
+                               w3 = __ldg(gl.j_w + e + 3 * G);
+                const JT v0 = Dv[w0 & 0xffffffu], v1 = Dv[w1 & 0xffffffu], v2 = Dv[w2 & 0xffffffu],
+                         v3 = Dv[w3 & 0xffffffu];
+                a0 = fma(coef(w0), v0, a0);
+                a1 = fma(coef(w1), v1, a1);
+                a0 = fma(coef(w2), v2, a0);
+                a1 = fma(coef(w3), v3, a1);
             }
+            for (; q < len; ++q, e += G) {
+                const unsigned wv = __ldg(gl.j_w + e);
+                a0 = fma(coef(wv), Dv[wv & 0xffffffu], a0);
+            }
+            J = fma(erow ? (JT)1 : (JT)__ldg(m.spf + s * kSpStride), a0 + a1, J);
         } else {
-            for (int e = e0; e < e1; ++e) J += (JT)__ldg(m.j_c + e) * sm.D[__ldg(m.j_d + e)];
+            for (; q + 4 <= len; q += 4, e += 4 * G) {
+                const int d0 = __ldg(gl.j_d + e), d1 = __ldg(gl.j_d + e + G), d2 = __ldg(gl.j_d + e + 2 * G),
+                          d3 = __ldg(gl.j_d + e + 3 * G);
+                const JT v0 = Dv[d0], v1 = Dv[d1], v2 = Dv[d2], v3 = Dv[d3];
+                a0 = fma((JT)__ldg(gl.j_c + e), v0, a0);
+                a1 = fma((JT)__ldg(gl.j_c + e + G), v1, a1);
+                a0 = fma((JT)__ldg(gl.j_c + e + 2 * G), v2, a0);
+                a1 = fma((JT)__ldg(gl.j_c + e + 3 * G), v3, a1);
+            }
+            for (; q < len; ++q, e += G) a0 = fma((JT)__ldg(gl.j_c + e), Dv[__ldg(gl.j_d + e)], a0);
+            J += a0 + a1;
         }
         sm.A[s * lda + k] = mh * J;
     }
-    const JT dTdeJ = (JT)dTde;
+    const JT dTdeJ = f32 ? (JT)dTdef : (JT)dTde;
     for (int s = sl; s < n; s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * dTdeJ);
     __syncwarp();
     for (int i = sl; i < n; i += G) sm.A[i * lda + i] += (JT)1;
@@ -501,7 +639,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         // solve for (delta rho, delta e / S), S = E_scale / rho: the energy
         // row and column then sit on the species' scale, which keeps the
         // FP32 elimination well conditioned
-        const JT S = (JT)escale, iS = (JT)(1.0 / escale);
+        const JT S = to_jt<JT>(escale), iS = (JT)1 / S;
         for (int k = sl; k < ns; k += G) {
             sm.A[ns * lda + k] *= iS;
             sm.A[k * lda + ns] *= S;
@@ -573,22 +711,42 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     // 8. update, convergence norm, and the linearised temperature of the
     //    new iterate (dT = (de - sum_s e_s^sens drho_s) / (rho cv)) as the
     //    next recovery's starting guess
+    //    (the FP32 path takes the norm's ratios in FP32: they decide
+    //    convergence, not the iterate)
     double nrm = 0.0, des = 0.0;
+    float nrmf = 0.f;
     int nonfinite = 0;
+    const float escf = f32 ? d2f_rz(escale) : 0.f;
     for (int i = sl; i < n; i += G) {
-        double d = (double)sm.A[i * lda + n];
-        if (f32 && i == ns) d *= escale;
+        float df = 0.f;
+        double d;
+        if (f32) {
+            df = (float)sm.A[i * lda + n];
+            if (i == ns) df *= escf;
+            d = f2d_alu(df);
+        } else {
+            d = (double)sm.A[i * lda + n];
+        }
         des += i < ns ? -sm.es[i] * d : d;
         const double xi = sm.x[i] + d;
         sm.x[i] = xi;
-        if (!isfinite(xi)) nonfinite = 1;
+        if (!finite_bits(xi)) nonfinite = 1;
         const double at = i < ns ? atol_rho : atol_e;
         const double den = fma(rtol, fabs(xi), at);
         // a zero scale counts a nonzero update as infinitely large
-        const double ri = den > 0.0 ? fabs(d) * frcp(den) : (d != 0.0 ? CUDART_INF : 0.0);
-        nrm = fmax(nrm, ri);
+        if (f32) {
+            const float denf = d2f_rz(den), adf = fabsf(df);
+            const float ri = denf > 0.f ? adf * __frcp_rn(denf) : (adf != 0.f ? CUDART_INF_F : 0.f);
+            nrmf = fmaxf(nrmf, ri);
+        } else {
+            const double ri = den > 0.0 ? fabs(d) * frcp(den) : (d != 0.0 ? CUDART_INF : 0.0);
+            nrm = fmax(nrm, ri);
+        }
     }
-    nrm = Grp<G>::max(nrm);
+    if (f32)
+        nrm = f2d_alu(Grp<G>::max(nrmf));
+    else
+        nrm = Grp<G>::max(nrm);
     nonfinite = Grp<G>::any(nonfinite);
     des = Grp<G>::sum(des);
     __syncwarp();
@@ -607,7 +765,7 @@ __global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, St
     const int sl = lane - slot * G;
     const int ns = m.ns, n = ns + 1;
     const double *tab = m.exp_tab;   // 2 KB, stays in L1
-    const long long sbytes = slot_bytes_for(ns, m.nr, m.nD, m.n_items, (int)sizeof(JT));
+    const long long sbytes = slot_bytes_for(m, (int)sizeof(JT));
     SlotMem<JT> sm;
     sm.carve(smem + (size_t)(warp * S + slot) * sbytes, m);
     // sentinel species: concentration 1, no Gibbs or enthalpy contribution
@@ -704,7 +862,7 @@ __global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, St
             if (!__any_sync(kFull, needT)) break;
             double Tr = T;
             bool ok = false;
-            recover_T<G>(m, sm.x, sl, needT, T, Tr, ok);
+            recover_T<G, sizeof(JT) == 4>(m, sm.x, sl, needT, T, Tr, ok);
             int neg = 0;
             for (int i = sl; i < ns; i += G)
                 if (sm.x[i] < -atol_rho) neg = 1;
