@@ -39,8 +39,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FFMA/clk x 2 x max clo
 def work_model(mech):
     """Algorithmic flops of one Newton iteration of one cell (FMA = 2, exp =
     EXP_FLOPS), from the mechanism's structure, split into the parts the
-    mixed-precision path keeps in FP64 and the Jacobian/LU parts it moves to
-    FP32 (all of it is FP64 on the FP64 path)."""
+    mixed-precision path keeps in FP64 and the parts it moves to FP32: the
+    Jacobian and LU, the heat capacities (they feed only dT/drho, dT/de and
+    the next temperature guess), the temperature recovery's derivative and
+    the convergence-norm ratios.  All of it is FP64 on the FP64 path."""
     ns, nr = mech.ns, mech.nr
     n = ns + 1
     nu = np.zeros((nr, ns), np.int64)
@@ -59,8 +61,8 @@ def work_model(mech):
         nD += len(cols)
         j_ent += len(cols) * rows
         sp_ent += rows
-    thermo = 38 * ns
-    t_recovery = 2 * 27 * ns
+    thermo, thermo_cp = 28 * ns, 10 * ns          # h, s, g, e | c_p, rho c_v
+    trec_e, trec_cv = 2 * 14 * ns, 2 * 13 * ns    # two recovery iterations: e(T) | c_v(T)
     rates_src = 30 * nr + 2 * nr * EXP_FLOPS     # rate constants, progress rates
     rates_jac = 10 * nr                          # C_M K_f, C_M K_b, dQ/dT
     d_entries = 8 * nD
@@ -68,10 +70,10 @@ def work_model(mech):
     gather_jac = 4 * sp_ent + 4 * ns
     jac = 6 * ns * n + 2 * j_ent + 2 * nD + 6 * n
     lu = sum(2 * (n - j - 1) * (n - j) + (n - j - 1) + 1 for j in range(n)) + n * n
-    update = 9 * n
-    fp64_core = thermo + t_recovery + rates_src + gather_src + update
-    jac_part = rates_jac + d_entries + gather_jac + jac + lu
-    return dict(flops=fp64_core + jac_part, mixed_fp64=fp64_core, mixed_fp32=jac_part,
+    update, update_norm = 6 * n, 3 * n
+    fp64_core = thermo + trec_e + rates_src + gather_src + update
+    fp32_side = thermo_cp + trec_cv + update_norm + rates_jac + d_entries + gather_jac + jac + lu
+    return dict(flops=fp64_core + fp32_side, mixed_fp64=fp64_core, mixed_fp32=fp32_side,
                 exp=2 * nr, nD=nD, j_ent=j_ent, lu=lu)
 
 
@@ -138,7 +140,7 @@ def barrier_max(world, value, device):
     return replicas.max_over_ranks(value, device) if world > 1 else value
 
 
-def cpu_baseline(sample_cells=4096, threads=None):
+def cpu_baseline(sample_cells=4096, threads=None, single=True):
     """The oracle on the host cores over a bounded, stratified sample of the
     workload (every 64th cell)."""
     import oracle
@@ -152,10 +154,19 @@ def cpu_baseline(sample_cells=4096, threads=None):
     t0 = time.perf_counter()
     _, _, out = om.advance_batch(rho, e, dt, T_in=fs.T, threads=threads)
     el = time.perf_counter() - t0
-    return dict(value=len(idx) / el, unit="cell-updates/s", cores=threads, kind="oracle",
-                sample="%d cells (every %dth of the 2^18-cell workload), one dt step each, %.1f s wall"
-                       % (len(idx), f.n // sample_cells, el),
-                newton_iters_mean=float(out["newton_iters"].mean()))
+    res = dict(value=len(idx) / el, unit="cell-updates/s", cores=threads, kind="oracle",
+               sample="%d cells (every %dth of the 2^18-cell workload), one dt step each, %.1f s wall"
+                      % (len(idx), f.n // sample_cells, el),
+               newton_iters_mean=float(out["newton_iters"].mean()))
+    if single:
+        # one host thread, the comparison point of the paper's single-core runs
+        n1 = max(1, sample_cells // 16)
+        t0 = time.perf_counter()
+        om.advance_batch(rho[:, :n1], e[:n1], dt, T_in=fs.T[:n1], threads=1)
+        el1 = time.perf_counter() - t0
+        res["single_thread"] = dict(value=n1 / el1, unit="cell-updates/s", cores=1,
+                                    sample="first %d of those cells, %.1f s wall" % (n1, el1))
+    return res
 
 
 def run_reference(args, world, rank):
@@ -165,7 +176,7 @@ def run_reference(args, world, rank):
     steps = []
     cb = None
     for i in range(args.warmup + args.steps):
-        res = cpu_baseline(sample_cells=args.ref_cells)
+        res = cpu_baseline(sample_cells=args.ref_cells, single=False)
         if i >= args.warmup:
             steps.append(res)
         cb = res
@@ -224,7 +235,8 @@ def time_path(torch, ch, rho0, e0, T_in, dt, precision, steps, warmup, flush, st
         stats = dict(status_ok=float((st == 0).float().mean().item()),
                      newton_iters=int(it.sum().item()),
                      newton_iters_mean=float(it.float().mean().item()),
-                     newton_iters_max=int(it.max().item()))
+                     newton_iters_max=int(it.max().item()),
+                     newton_iters_hist=torch.bincount(it.clamp(0, 64).long(), minlength=65).tolist())
     return tot, ker, stats
 
 
@@ -267,7 +279,7 @@ def serving_run(torch, chem, synth, device, n_requests, rate_frac=0.7, budget_by
     # capacity: a saturating burst
     done = []
     t0 = time.perf_counter()
-    burst = 24
+    burst = 64
     for j in range(burst):
         k = j % 2
         i = pick(k, rng.uniform())
@@ -319,6 +331,26 @@ def serving_run(torch, chem, synth, device, n_requests, rate_frac=0.7, budget_by
             "failed": st["failed"]}
 
 
+def serving_sweep(args):
+    """The request stream at several loads (fractions of the measured
+    capacity, overload included) and HBM budgets (one small enough to force
+    queueing); one JSON line with a record per run."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1110_4903_gb300 import chem, synth
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    runs = []
+    for frac in (0.5, 0.8, 1.0, 1.3):
+        runs.append(serving_run(torch, chem, synth, device, args.serving_requests, frac, 0))
+    # the largest request (2^18 cells, 36 species) holds about 80 MB
+    for budget in (256 << 20, 96 << 20):
+        runs.append(serving_run(torch, chem, synth, device, args.serving_requests, 0.7, budget))
+    print(json.dumps({"metric": "request latency of the chemistry server (Poisson arrivals)",
+                      "unit": "ms", "requests_per_run": args.serving_requests, "runs": runs}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,11 +372,17 @@ def main():
                     help="requests in the serving stream (0: skip the serving run)")
     ap.add_argument("--serving-rate", type=float, default=0.7, help="load as a fraction of capacity")
     ap.add_argument("--serving-budget", type=int, default=0, help="server HBM budget in bytes")
+    ap.add_argument("--serving-sweep", action="store_true",
+                    help="only the request server: loads 0.5-1.2 of capacity and two HBM budgets")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.serving_sweep:
+        if rank == 0:
+            serving_sweep(args)
         return
 
     import torch
@@ -426,6 +464,9 @@ def main():
                              newton_iters_mean=stats["newton_iters_mean"],
                              newton_iters_max=stats["newton_iters_max"],
                              cells_ok=stats["status_ok"], roofline=roof)
+        if args.workload != WORKLOAD:
+            # Newton iterations per cell: histogram over 0..63, 64 = 64 or more
+            results[name]["newton_iters_hist"] = stats["newton_iters_hist"]
         if ch is head:
             clk = ck.summary()
             gpu_launches = launches
