@@ -100,13 +100,16 @@ typedef struct chem_options {
                                  FP32 LU makes convergence linear; 1..1000 */
     double  conv_kappa;       /* > 0: also converged when the contraction theta = norm_k/norm_k-1 < 1
                                  bounds the remaining error, theta/(1-theta) norm_k <= conv_kappa
-                                 (Hairer & Wanner's stopping estimate); 0 = off; 0..1 */
+                                 (Hairer & Wanner's stopping estimate); 0 = off; 0..1.  CHEM_FP64 */
+    double  conv_kappa_mixed; /* the same for the CHEM_MIXED path */
 } chem_options;
 
 /* Fills *o with the defaults: FP64, rtol 1e-10, atol_rel 1e-12,
  * max_newton 12, max_halvings 20, max_attempts 1000, point_implicit 0,
  * div_check 1, lanes_per_cell 0, autotune 0, hbm_budget_bytes 0,
- * max_newton_mixed 12, conv_kappa 0.01. */
+ * max_newton_mixed 12, conv_kappa 0 (the FP64 path stops on the norm test alone: an
+ * accepted update well above the tolerance carries its rounding into the result),
+ * conv_kappa_mixed 0.01. */
 int chem_default_options(chem_options *o);
 
 /* Validates the mechanism (index ranges, 1..3 species per side with

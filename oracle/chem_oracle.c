@@ -530,7 +530,7 @@ void om_default_opts(om_opts *o)
     o->max_attempts = 1000;
     o->point_implicit = 0;
     o->div_check = 1;
-    o->conv_kappa = 0.01;
+    o->conv_kappa = 0.0;
 }
 
 /* ---------------------------------------------------------------------------

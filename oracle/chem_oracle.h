@@ -51,7 +51,8 @@ typedef struct om_opts {
     int point_implicit;   /* 1: one linearised step per substep, Eq. 29 as printed */
     int div_check;        /* 1: abandon a substep whose Newton norm stops falling */
     double conv_kappa;    /* > 0: also accept when the contraction rate bounds the error
-                             still left by conv_kappa (Hairer & Wanner's safety factor); 0: off */
+                             still left by conv_kappa (Hairer & Wanner's safety factor); 0 (the
+                             default): the norm test alone */
 } om_opts;
 
 /* Per-cell status codes. */

@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("point_implicit", C.c_int32), ("div_check", C.c_int32),
                 ("lanes_per_cell", C.c_int32), ("autotune", C.c_int32),
                 ("hbm_budget_bytes", C.c_int64), ("max_newton_mixed", C.c_int32),
-                ("conv_kappa", C.c_double)]
+                ("conv_kappa", C.c_double), ("conv_kappa_mixed", C.c_double)]
 
 
 class AdvanceArgs(C.Structure):

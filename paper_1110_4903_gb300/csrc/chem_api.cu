@@ -677,7 +677,8 @@ int launch_cfg(Handle *h, const chem_advance_args *a, int prec, const LaunchCfg 
     cudaStream_t st = (cudaStream_t)a->stream;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "zeroing the work counter");
-    StepOptions o{h->opts.rtol, h->opts.atol_rel, h->opts.conv_kappa,
+    StepOptions o{h->opts.rtol, h->opts.atol_rel,
+                  prec == CHEM_MIXED ? h->opts.conv_kappa_mixed : h->opts.conv_kappa,
                   prec == CHEM_MIXED ? h->opts.max_newton_mixed : h->opts.max_newton,
                   h->opts.max_halvings, h->opts.max_attempts, h->opts.point_implicit,
                   h->opts.div_check};
@@ -725,7 +726,8 @@ int chem_default_options(chem_options *o) {
     o->autotune = 0;
     o->hbm_budget_bytes = 0;
     o->max_newton_mixed = 12;
-    o->conv_kappa = 0.01;
+    o->conv_kappa = 0.0;
+    o->conv_kappa_mixed = 0.01;
     return CHEM_OK;
 }
 
@@ -744,6 +746,8 @@ static int check_options(const chem_options *o) {
         return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d (0, 2, 4, 8, 16 or 32)", l);
     if (o->hbm_budget_bytes < 0) return fail(CHEM_E_INVALID_ARG, "hbm_budget_bytes");
     if (!(o->conv_kappa >= 0.0 && o->conv_kappa <= 1.0)) return fail(CHEM_E_INVALID_ARG, "conv_kappa");
+    if (!(o->conv_kappa_mixed >= 0.0 && o->conv_kappa_mixed <= 1.0))
+        return fail(CHEM_E_INVALID_ARG, "conv_kappa_mixed");
     return CHEM_OK;
 }
 

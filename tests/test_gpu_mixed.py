@@ -44,7 +44,7 @@ def test_mixed_against_oracle(torch, wl, ncell, opts):
     fs = synth.subsample(f, idx)
     rho, e = P.initial_state(m, fs)
     c = chem.Chem(m, precision=chem.MIXED, **opts)
-    rr, er, oo = P.oracle_reference(m, rho, e, dt, fs.T, threads=THREADS, **opts)
+    rr, er, oo = P.oracle_reference(m, rho, e, dt, fs.T, threads=THREADS, **opts, **P.MIXED_OPTS)
     rg, eg, og = P.gpu_run(torch, c, rho, e, dt, T_in=fs.T)
     st = _stats(rg, eg, og, rr, er, oo, rho)
     print(wl, st)

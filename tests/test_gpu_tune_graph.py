@@ -47,7 +47,7 @@ def test_autotune_then_parity(torch, front):
     assert np.array_equal(r.cpu().numpy(), rho)        # the tuner worked on a copy
     # parity of the tuned shape on a sample containing band cells
     idx = np.concatenate([np.arange(0, rho.shape[1], 811)[:40], np.where(fs.T > 2500)[0][:40]])
-    rr, er, oo = P.oracle_reference(m, rho[:, idx], e[idx], dt, fs.T[idx], threads=THREADS)
+    rr, er, oo = P.oracle_reference(m, rho[:, idx], e[idx], dt, fs.T[idx], threads=THREADS, **P.MIXED_OPTS)
     rg, eg, og = P.gpu_run(torch, c, rho[:, idx], e[idx], dt, T_in=fs.T[idx])
     same = (og["substeps"] == oo["substeps"]) & (og["failures"] == oo["failures"])
     rel = P.rel_species(rg, rr, rho[:, idx].sum(0))
