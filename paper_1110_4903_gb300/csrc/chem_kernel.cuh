@@ -116,6 +116,26 @@ __device__ __forceinline__ bool finite_bits(double v) {
     return ((unsigned)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffu) != 0x7ffu;
 }
 
+// Argmax over a whole warp (one cell per warp) with redux.sync: the largest
+// key, the lowest index on ties, as the shuffle tree gives it.  FP64 keys
+// take the high word, then the low word among the lanes holding the high
+// maximum; FP32 keys (abs bits << 29) fit one word.
+template <typename JT>
+__device__ __forceinline__ void warp_argmax(unsigned long long &k, int &i) {
+    if (sizeof(JT) == 4) {
+        const unsigned k32 = (unsigned)(k >> 29);
+        const unsigned m = __reduce_max_sync(kFull, k32);
+        i = (int)__reduce_min_sync(kFull, k32 == m ? (unsigned)i : 0xffffffffu);
+        k = (unsigned long long)m << 29;
+    } else {
+        const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+        const unsigned mhi = __reduce_max_sync(kFull, hi);
+        const unsigned mlo = __reduce_max_sync(kFull, hi == mhi ? lo : 0u);
+        i = (int)__reduce_min_sync(kFull, (hi == mhi && lo == mlo) ? (unsigned)i : 0xffffffffu);
+        k = ((unsigned long long)mhi << 32) | mlo;
+    }
+}
+
 // |v| as an ordered integer key (NaN maps to 0 so it is never the pivot).
 __device__ __forceinline__ unsigned long long abs_key(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
@@ -141,7 +161,13 @@ __device__ __forceinline__ double frcp(double a) {
     e = fma(-a, r, 1.0);
     return fma(r, e, r);
 }
-__device__ __forceinline__ float frcp(float a) { return __frcp_rn(a); }
+// FP32 reciprocal of the pivot: the hardware approximation (within an ulp or
+// two), enough for an elimination whose result Newton refines in FP64.
+__device__ __forceinline__ float frcp(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 
 // The library exp for the arguments the table path does not take; kept out
 // of line so its code is not repeated at every call site.
@@ -662,7 +688,10 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
                 bi = i;
             }
         }
-        Grp<G>::argmax(best, bi);
+        if constexpr (G == 32)
+            warp_argmax<JT>(best, bi);
+        else
+            Grp<G>::argmax(best, bi);
         if (best == 0 || key_is_inf(best, JT(0))) sing = true;
         if (bi != j && bi < n) {
             for (int k = j + sl; k <= n; k += G) {
