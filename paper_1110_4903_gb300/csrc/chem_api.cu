@@ -166,14 +166,14 @@ static void third_body_first(const chem_mech_desc *in, ReorderedMech &o) {
 struct HostTables {
     std::vector<double> thermo, tmid, tpoly, sp, rxn_d, eff_c, d_c, j_c, sp_nu, exp_tab;
     std::vector<float> tpoly_f;
-    std::vector<float> rxn_df, d_cef, d_ef, spf;
+    std::vector<float> rxn_df, d_cef, spf;
     std::vector<int4> d_pk;
     std::vector<unsigned> j_w, sp_w;
     std::vector<int> rxn_f, eff_ptr, eff_sp, d_i0, d_i1, j_sk, j_ptr, j_d, it_ptr, sp_item_ptr, sp_r;
     std::vector<int2> j_meta;
-    std::vector<int> j_nu, sp_nui;
+    std::vector<int> j_nu, sp_nui, j_sk32, j_ptr32, j_d32;
     struct Layout {
-        std::vector<int2> j_meta, it_meta;
+        std::vector<int2> j_meta, j_meta32, it_meta;
         std::vector<unsigned> j_w, sp_w;
         std::vector<int> j_d;
         std::vector<double> j_c, sp_nu;
@@ -340,12 +340,16 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
             if (v != 0) lists[(size_t)s * ns + k].push_back({j, v * d->molar_mass[s], v});
         }
         if (de[r] != 0.0) lists[(size_t)ns * ns + k].push_back({j, -de[r], 0});
-        t.d_ef.push_back((float)-de[r]);
     }
-    std::vector<int> order((ns + 1) * ns);
+    // FP64 lists: every entry, longest list first.  FP32 lists: the species
+    // entries only (the FP32 kernel forms the energy row from the species
+    // rows), longest first.
+    auto longer = [&](int a, int b) { return lists[a].size() > lists[b].size(); };
+    std::vector<int> order((ns + 1) * ns), order32(ns * ns);
     for (int i = 0; i < (ns + 1) * ns; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return lists[a].size() > lists[b].size(); });
+    for (int i = 0; i < ns * ns; ++i) order32[i] = i;
+    std::stable_sort(order.begin(), order.end(), longer);
+    std::stable_sort(order32.begin(), order32.end(), longer);
     t.nJ = (ns + 1) * ns;
     t.j_ptr.push_back(0);
     for (int idx : order) {
@@ -354,9 +358,18 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         for (const auto &tm : lists[idx]) {
             t.j_d.push_back(tm.j);
             t.j_c.push_back(tm.c);
-            t.j_nu.push_back(tm.nu);
         }
         t.j_ptr.push_back((int)t.j_d.size());
+    }
+    t.j_ptr32.push_back(0);
+    for (int idx : order32) {
+        const int s = idx / ns, k = idx % ns;
+        t.j_sk32.push_back((s << 8) | k);
+        for (const auto &tm : lists[idx]) {
+            t.j_d32.push_back(tm.j);
+            t.j_nu.push_back(tm.nu);
+        }
+        t.j_ptr32.push_back((int)t.j_d32.size());
     }
     // species lists (reactions with nu_rs != 0) in chunks of kChunk
     t.sp_item_ptr.assign(ns + 1, 0);
@@ -400,7 +413,7 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     }
     // a term's word: D index (or reaction) in bits 0..23, nu_rs in 24..31
     auto word = [](int i, int nu) { return (unsigned)i | ((unsigned)(nu & 0xff) << 24); };
-    for (size_t e = 0; e < t.j_d.size(); ++e) t.j_w.push_back(word(t.j_d[e], t.j_nu[e]));
+    for (size_t e = 0; e < t.j_d32.size(); ++e) t.j_w.push_back(word(t.j_d32[e], t.j_nu[e]));
     for (size_t e = 0; e < t.sp_r.size(); ++e) t.sp_w.push_back(word(t.sp_r[e], t.sp_nui[e]));
     // the gather layouts for each lane count (chem_internal.h): list p on
     // lane p % G of pass p / G, its q-th term at base(pass) + q G + lane
@@ -426,14 +439,15 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         auto &L = t.lay[li];
         std::vector<int> pos;
         const int nw = interleave(t.nJ, t.j_ptr, G, L.j_meta, pos, 16, &t.j_sk);
-        L.j_w.assign(std::max(nw, 1), 0u);
         L.j_d.assign(std::max(nw, 1), 0);
         L.j_c.assign(std::max(nw, 1), 0.0);
         for (size_t e = 0; e < pos.size(); ++e) {
-            L.j_w[pos[e]] = t.j_w[e];
             L.j_d[pos[e]] = t.j_d[e];
             L.j_c[pos[e]] = t.j_c[e];
         }
+        const int nw32 = interleave(ns * ns, t.j_ptr32, G, L.j_meta32, pos, 16, &t.j_sk32);
+        L.j_w.assign(std::max(nw32, 1), 0u);
+        for (size_t e = 0; e < pos.size(); ++e) L.j_w[pos[e]] = t.j_w[e];
         const int ni = interleave(t.n_items, t.it_ptr, G, L.it_meta, pos, 0, nullptr);
         L.sp_w.assign(std::max(ni, 1), 0u);
         L.sp_nu.assign(std::max(ni, 1), 0.0);
@@ -446,7 +460,7 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     for (double v : t.sp) t.spf.push_back((float)v);
     // keep every array non-empty so device pointers are valid
     auto pad_f = [](std::vector<float> &v) { if (v.empty()) v.push_back(0.0f); };
-    pad_f(t.rxn_df); pad_f(t.d_cef); pad_f(t.d_ef);
+    pad_f(t.rxn_df); pad_f(t.d_cef);
     if (t.d_pk.empty()) t.d_pk.push_back(make_int4(0, 0, 0, 0));
     auto pad_u = [](std::vector<unsigned> &v) { if (v.empty()) v.push_back(0u); };
     pad_u(t.j_w); pad_u(t.sp_w);
@@ -473,10 +487,11 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
                  i_rf = addv(t.rxn_f), i_ep = addv(t.eff_ptr), i_es = addv(t.eff_sp), i_ec = addv(t.eff_c),
                  i_dpk = addv(t.d_pk), i_dc = addv(t.d_c), i_sip = addv(t.sp_item_ptr),
                  i_ex = addv(t.exp_tab), i_rdf = addv(t.rxn_df), i_dcef = addv(t.d_cef),
-                 i_def = addv(t.d_ef), i_spf = addv(t.spf);
-    size_t i_lay[kLayouts][7];
+                 i_spf = addv(t.spf);
+    size_t i_lay[kLayouts][8];
     for (int li = 0; li < kLayouts; ++li) {
         const auto &L = t.lay[li];
+        i_lay[li][7] = addv(L.j_meta32);
         i_lay[li][0] = addv(L.j_meta);
         i_lay[li][1] = addv(L.j_w);
         i_lay[li][2] = addv(L.j_d);
@@ -519,6 +534,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     for (int li = 0; li < kLayouts; ++li) {
         GatherLayout &g = m.gl[li];
         g.j_meta = (const int2 *)at(i_lay[li][0]);
+        g.j_meta32 = (const int2 *)at(i_lay[li][7]);
         g.j_w = (const unsigned *)at(i_lay[li][1]);
         g.j_d = (const int *)at(i_lay[li][2]);
         g.j_c = (const double *)at(i_lay[li][3]);
@@ -531,7 +547,6 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     m.exp_tab = (const double *)at(i_ex);
     m.rxn_df = (const float *)at(i_rdf);
     m.d_cef = (const float *)at(i_dcef);
-    m.d_ef = (const float *)at(i_def);
 
     m.spf = (const float *)at(i_spf);
     return CHEM_OK;

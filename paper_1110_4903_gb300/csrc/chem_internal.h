@@ -72,13 +72,18 @@ constexpr int kExpTab = 256;
 // sits at word base + q G + lane, where base is the pass's first word, so the
 // lanes of a pass read their q-th terms from consecutive words (one cache
 // line per warp load instead of one per lane).
-//   j_meta[p]  = {first word of entry p, k | s << 8 | terms << 16}
-//   j_w        = D index | nu_rs << 24 (species rows), D index (energy row)
-//   j_d, j_c   = D index and FP64 coefficient nu_rs M_s (or -de_r)
+//   FP64 kernel: every Jacobian entry, longest list first
+//     j_meta[p]   = {first word of entry p, k | s << 8 | terms << 16}
+//     j_d, j_c    = D index and coefficient nu_rs M_s (energy row: -de_r)
+//   FP32 kernel: the ns*ns species entries, longest list first (it forms the
+//   energy row from the species rows)
+//     j_meta32[p] = as j_meta
+//     j_w         = D index | nu_rs << 24 (the row's M_s multiplies the sum)
 //   it_meta[i] = {first word of item i, entries}
 //   sp_w       = r | nu_rs << 24;  sp_nu = nu_rs (FP64)
 struct GatherLayout {
     const int2 *j_meta;
+    const int2 *j_meta32;
     const unsigned *j_w;
     const int *j_d;
     const double *j_c;
@@ -95,7 +100,8 @@ struct DeviceMech {
     int ns, nr;
     int ntb;                    // third-body reactions: the first ntb (internal order)
     int nD, nD_F, nD_B, nD_FB;  // group ends: [0,F) [F,B) [B,FB) [FB,nD)
-    int nJ;                     // Jacobian entries gathered: ns*ns species, ns energy-row
+    int nJ;                     // Jacobian entries gathered by the FP64 kernel: ns*ns species,
+                                // ns energy row (the FP32 kernel gathers the ns*ns species)
     int n_items;                // species-gather work items
     const double *thermo;       // [ns][2][16]
     const double *tmid;         // [ns] (positive: compared as integers)
@@ -118,7 +124,6 @@ struct DeviceMech {
     // FP32 copies for the mixed-precision Jacobian
     const float *rxn_df;        // [nr][4] beta, Ea/R, sum nu, 0
     const float *d_cef;         // [nD] efficiency coefficient in FP32
-    const float *d_ef;          // [nD] energy-row coefficient of the D entry's reaction
     const float *spf;           // [ns][4] M, 1/M, R/M, e_f in FP32
 };
 

@@ -51,9 +51,15 @@ struct Grp {
         return v;
     }
     __device__ __forceinline__ static int any(int v) {
+        if (G == 32) return __any_sync(kFull, v);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
         return v;
+    }
+    // maximum of non-negative floats (their bit patterns order the same way)
+    __device__ __forceinline__ static float max_nonneg(float v) {
+        if (G == 32) return __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(v)));
+        return max(v);
     }
     // largest key, lowest index on ties
     __device__ __forceinline__ static void argmax(unsigned long long &k, int &i) {
@@ -537,12 +543,14 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         Ue += efJ * us;
     }
     wde = Grp<G>::sum(wde);
-    We = Grp<G>::sum(We);
-    Ue = Grp<G>::sum(Ue);
-    // the energy row's rank-one parts: J_ek = -sum_s e_f,s J_sk
-    if (sl == 0) {
-        sm.w[ns] = -We;
-        sm.u[ns] = -Ue;
+    if (!f32) {
+        // the energy row's rank-one parts: J_ek = -sum_s e_f,s J_sk
+        We = Grp<G>::sum(We);
+        Ue = Grp<G>::sum(Ue);
+        if (sl == 0) {
+            sm.w[ns] = -We;
+            sm.u[ns] = -Ue;
+        }
     }
     __syncwarp();
 
@@ -613,8 +621,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     //    (four terms in flight per trip, two accumulators)
     const JT mh = to_jt<JT>(-h);
     const JT *__restrict__ Dv = sm.D;
-    for (int p = sl; p < m.nJ; p += G) {
-        const int2 meta = __ldg(gl.j_meta + p);
+    for (int p = sl; p < (f32 ? ns * ns : m.nJ); p += G) {
+        const int2 meta = __ldg((f32 ? gl.j_meta32 : gl.j_meta) + p);
         const int len = meta.y >> 16;
         const int s = (meta.y >> 8) & 0xff, k = meta.y & 0xff;
         const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
@@ -622,11 +630,9 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         JT a0 = 0, a1 = 0;
         int e = meta.x, q = 0;
         if (f32) {
-            // species row: M_s sum nu_rs D_rk; energy row: sum (-de_r) D_rk
-            const bool erow = s == ns;
-            auto coef = [&](unsigned wv) -> JT {
-                return erow ? (JT)__ldg(m.d_ef + (wv & 0xffffffu)) : (JT)small_int_to_float((int)wv >> 24);
-            };
+            // species row: M_s sum nu_rs D_rk (the energy row follows from
+            // the species rows below)
+            auto coef = [](unsigned wv) -> JT { return (JT)small_int_to_float((int)wv >> 24); };
             for (; q + 4 <= len; q += 4, e += 4 * G) {
                 const unsigned w0 = __ldg(gl.j_w + e), w1 = __ldg(gl.j_w + e + G), w2 = __ldg(gl.j_w + e + 2 * G),
                                w3 = __ldg(gl.j_w + e + 3 * G);
@@ -641,7 +647,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
                 const unsigned wv = __ldg(gl.j_w + e);
                 a0 = fma(coef(wv), Dv[wv & 0xffffffu], a0);
             }
-            J = fma(erow ? (JT)1 : (JT)__ldg(m.spf + s * kSpStride), a0 + a1, J);
+            J = fma((JT)__ldg(m.spf + s * kSpStride), a0 + a1, J);
         } else {
             for (; q + 4 <= len; q += 4, e += 4 * G) {
                 const int d0 = __ldg(gl.j_d + e), d1 = __ldg(gl.j_d + e + G), d2 = __ldg(gl.j_d + e + 2 * G),
@@ -658,8 +664,25 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         sm.A[s * lda + k] = mh * J;
     }
     const JT dTdeJ = f32 ? (JT)dTdef : (JT)dTde;
-    for (int s = sl; s < n; s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * dTdeJ);
+    for (int s = sl; s < (f32 ? ns : n); s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * dTdeJ);
     __syncwarp();
+    if (f32) {
+        // energy row -h J_ek = -sum_s e_f,s (-h J_sk): column sums over the
+        // species rows, four partial sums in flight per lane
+        for (int k = sl; k < n; k += G) {
+            JT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            int s = 0;
+            for (; s + 4 <= ns; s += 4) {
+                a0 = fma((JT)__ldg(m.spf + s * kSpStride + 3), sm.A[s * lda + k], a0);
+                a1 = fma((JT)__ldg(m.spf + (s + 1) * kSpStride + 3), sm.A[(s + 1) * lda + k], a1);
+                a2 = fma((JT)__ldg(m.spf + (s + 2) * kSpStride + 3), sm.A[(s + 2) * lda + k], a2);
+                a3 = fma((JT)__ldg(m.spf + (s + 3) * kSpStride + 3), sm.A[(s + 3) * lda + k], a3);
+            }
+            for (; s < ns; ++s) a0 = fma((JT)__ldg(m.spf + s * kSpStride + 3), sm.A[s * lda + k], a0);
+            sm.A[ns * lda + k] = -((a0 + a1) + (a2 + a3));
+        }
+        __syncwarp();
+    }
     for (int i = sl; i < n; i += G) sm.A[i * lda + i] += (JT)1;
     if (f32) {
         // solve for (delta rho, delta e / S), S = E_scale / rho: the energy
@@ -773,7 +796,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         }
     }
     if (f32)
-        nrm = f2d_alu(Grp<G>::max(nrmf));
+        nrm = f2d_alu(Grp<G>::max_nonneg(nrmf));
     else
         nrm = Grp<G>::max(nrm);
     nonfinite = Grp<G>::any(nonfinite);
