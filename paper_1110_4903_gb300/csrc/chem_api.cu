@@ -567,7 +567,7 @@ int configure(Handle *h, int prec, int G, int wpb_req, LaunchCfg &cfg) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)h->max_smem_optin);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    for (int wpb = 8; wpb >= 1; --wpb) {
+    for (int wpb = kMaxBlockThreads / 32; wpb >= 1; --wpb) {
         if (wpb_req && wpb != wpb_req) continue;
         const long long smem = kBlockHeaderBytes + (long long)wpb * S * sb;
         if (smem > h->max_smem_optin) continue;

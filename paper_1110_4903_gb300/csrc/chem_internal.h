@@ -54,6 +54,9 @@ constexpr int kRxnFStride = 2;
 // Species-gather chunk length (entries per work item).
 constexpr int kChunk = 8;
 
+// Threads per block of the step kernel at most (its launch bounds).
+constexpr int kMaxBlockThreads = 192;
+
 // Entries of the exp table (2^(j/kExpTab)).
 constexpr int kExpTab = 256;
 
@@ -154,38 +157,42 @@ enum CellStatus { kCellOk = 0, kCellNewtonFailed = 1, kCellTFailed = 2, kCellBad
 // exp table is read through L1).
 constexpr int kBlockHeaderBytes = 0;
 
-// The D region of a slot holds the nD D entries (Jacobian type) and, earlier
-// in each Newton iteration, the species-gather partial sums (3 doubles per
-// work item); its size in 8-byte units:
-__host__ __device__ inline int dreg8_for(int nD, int n_items, int jt) {
-    const int a = (nD * jt + 7) / 8, b = 3 * n_items;
-    return a > b ? a : b;
+// Bytes of one cell slot, in this order (jt = sizeof of the Jacobian type):
+//   doubles   x, x0 (n each); c, gRT with a sentinel (ns+1 each); FP64 path
+//             also hRT (ns+1, with the sentinel) and es (ns)
+//   JT        FP64 path: dTdr (ns), w, u (ns+1 each: the species rows' T
+//             derivative and third-body vectors, then the energy row's), rhs (n)
+//             FP32 path: w, u (ns each), cJ, hJ (ns+1 each: c and h/RT with the
+//             sentinel), es (ns), rhs (n)
+//   D region  first Q (nr doubles) and the species-gather partial sums (per
+//             item: sum nu Q in FP64, then sum nu dQ/dT and sum nu q_tb in JT),
+//             which are dead once the D entries (nD in JT) are written
+//   union     the per-reaction values dQdT, A1, A2 (nr JT each) and qtb (ntb
+//             JT), dead once the D entries exist, and the augmented matrix
+//             n x (n+1) in JT, which is written after that
+__host__ __device__ inline long long align16(long long b) { return (b + 15) / 16 * 16; }
+__host__ __device__ inline long long slot_dbl_bytes(int ns, int jt) {
+    const int n = ns + 1;
+    return align16((2LL * n + 2LL * (ns + 1) + (jt == 8 ? (long long)(ns + 1) + ns : 0)) * 8);
 }
-
-// Bytes of one cell slot, in this order:
-//   doubles  x, x0 (n each); c, hRT, gRT with a sentinel (ns+1 each); es, wd (ns each)
-//   JT       dTdr (ns); w, u (ns+1 each: the species rows' T-derivative and
-//            third-body vectors, then the energy row's); for FP32 also c and
-//            hRT copies (ns+1 each)
-//   D region dreg8 * 8 bytes
-//   union    the per-reaction values Q (double), dQdT, A1, A2 (JT) and the
-//            third-body progress qtb (JT, ntb entries), dead once the D
-//            entries exist, and the augmented matrix n x (n+1) in JT, which
-//            is written after that
 __host__ __device__ inline long long slot_small_bytes(int ns, int jt) {
-    const long long cnt = 3LL * ns + 2 + (jt == 4 ? 2LL * (ns + 1) : 0);
-    return (cnt * jt + 15) / 16 * 16;
+    const int n = ns + 1;
+    const long long cnt = jt == 8 ? (long long)ns + 2LL * (ns + 1) + n : 2LL * ns + 2LL * (ns + 1) + ns + n;
+    return align16(cnt * jt);
+}
+__host__ __device__ constexpr long long item_bytes(int jt) { return 8 + 2LL * jt; }
+__host__ __device__ inline long long slot_dreg_bytes(int nr, int nD, int n_items, int jt) {
+    const long long a = (long long)nD * jt, b = (long long)nr * 8 + (long long)n_items * item_bytes(jt);
+    return align16(a > b ? a : b);
 }
 __host__ __device__ inline long long slot_union_bytes(int ns, int nr, int ntb, int jt) {
     const int n = ns + 1;
-    const long long a = (long long)nr * 8 + 3LL * nr * jt + (long long)ntb * jt, b = (long long)n * (n + 1) * jt;
-    return ((a > b ? a : b) + 15) / 16 * 16;
+    const long long a = 3LL * nr * jt + (long long)ntb * jt, b = (long long)n * (n + 1) * jt;
+    return align16(a > b ? a : b);
 }
 __host__ __device__ inline long long slot_bytes_for(const DeviceMech &m, int jt) {
-    const int ns = m.ns, n = ns + 1;
-    const long long dbl = (2LL * n + 3LL * (ns + 1) + 2LL * ns) * 8;
-    const long long dreg = ((long long)dreg8_for(m.nD, m.n_items, jt) * 8 + 15) / 16 * 16;
-    return (dbl + 15) / 16 * 16 + slot_small_bytes(ns, jt) + dreg + slot_union_bytes(ns, m.nr, m.ntb, jt);
+    return slot_dbl_bytes(m.ns, jt) + slot_small_bytes(m.ns, jt) + slot_dreg_bytes(m.nr, m.nD, m.n_items, jt) +
+           slot_union_bytes(m.ns, m.nr, m.ntb, jt);
 }
 
 }  // namespace chem

@@ -331,9 +331,12 @@ __device__ __forceinline__ void lu_update_by_columns(JT *A, int lda, int n, int 
 
 template <typename JT>
 struct SlotMem {
-    double *x, *x0, *c, *hRT, *gRT, *es, *wd, *Q, *part;
-    JT *D, *dTdr, *w, *u, *A, *dQdT, *qtb, *A1, *A2;
-    JT *cJ, *hJ;   // concentrations and h/RT in the Jacobian type (FP32 path)
+    double *x, *x0, *c, *hRT, *gRT, *es, *Q, *part;
+    JT *D, *dTdr, *w, *u, *A, *dQdT, *qtb, *A1, *A2, *rhs;
+    JT *cJ, *hJ, *esJ;   // FP32 path: c, h/RT and e^sens in the Jacobian type
+    // layout and sizes in chem_internal.h (slot_bytes_for); the FP64 path has
+    // no FP32 copies (cJ = c, hJ = hRT) and the FP32 path no FP64 hRT, es
+    // or dTdr
     __device__ __forceinline__ void carve(char *base, const DeviceMech &m) {
         const int ns = m.ns, n = ns + 1, nr = m.nr;
         constexpr int jt = (int)sizeof(JT);
@@ -341,28 +344,40 @@ struct SlotMem {
         x = p;
         x0 = x + n;
         c = x0 + n;
-        hRT = c + ns + 1;
-        gRT = hRT + ns + 1;
-        es = gRT + ns + 1;
-        wd = es + ns;
-        char *q = base + ((2LL * n + 3LL * (ns + 1) + 2LL * ns) * 8 + 15) / 16 * 16;
-        dTdr = reinterpret_cast<JT *>(q);
-        w = dTdr + ns;
-        u = w + ns + 1;
-        if (jt == 4) {
-            cJ = u + ns + 1;
-            hJ = cJ + ns + 1;
+        gRT = c + ns + 1;
+        if (jt == 8) {
+            hRT = gRT + ns + 1;
+            es = hRT + ns + 1;
         } else {
+            hRT = es = nullptr;
+        }
+        char *q = base + slot_dbl_bytes(ns, jt);
+        JT *t = reinterpret_cast<JT *>(q);
+        if (jt == 8) {
+            dTdr = t;
+            w = dTdr + ns;
+            u = w + ns + 1;
+            rhs = u + ns + 1;
             cJ = reinterpret_cast<JT *>(c);
             hJ = reinterpret_cast<JT *>(hRT);
+            esJ = reinterpret_cast<JT *>(es);
+        } else {
+            dTdr = nullptr;
+            w = t;
+            u = w + ns;
+            cJ = u + ns;
+            hJ = cJ + ns + 1;
+            esJ = hJ + ns + 1;
+            rhs = esJ + ns;
         }
         q += slot_small_bytes(ns, jt);
-        part = reinterpret_cast<double *>(q);
-        D = reinterpret_cast<JT *>(q);
-        q += ((long long)dreg8_for(m.nD, m.n_items, jt) * 8 + 15) / 16 * 16;
-        // union: per-reaction rates, then (after the D entries) the matrix
+        // D region: Q and the gather partials until the D entries replace them
         Q = reinterpret_cast<double *>(q);
-        dQdT = reinterpret_cast<JT *>(Q + nr);
+        part = Q + nr;
+        D = reinterpret_cast<JT *>(q);
+        q += slot_dreg_bytes(nr, m.nD, m.n_items, jt);
+        // union: per-reaction values, then (after the D entries) the matrix
+        dQdT = reinterpret_cast<JT *>(q);
         A1 = dQdT + nr;
         A2 = A1 + nr;
         qtb = A2 + nr;
@@ -401,10 +416,10 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const double hRT = th[0] + T * (th[5] + T * (th[6] + T * (th[7] + T * th[8]))) + th[9] * invT;
         const double sR = nasa_s(th, T, lnT);
         const double RM = __ldg(spr + 2);
-        sm.hRT[s] = hRT;
         sm.gRT[s] = hRT - sR;
-        sm.es[s] = RM * T * (hRT - 1.0) - __ldg(spr + 3);
+        const double es = RM * T * (hRT - 1.0) - __ldg(spr + 3);
         if (f32) {
+            sm.esJ[s] = to_jt<JT>(es);
             const float *d = m.tpoly_f + (size_t)row * kTpolyFStride;
             const float cv = fmaf(fmaf(fmaf(fmaf(__ldg(d + 4), Tf, __ldg(d + 3)), Tf, __ldg(d + 2)), Tf, __ldg(d + 1)),
                                   Tf, __ldg(d));
@@ -416,6 +431,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             const double cv = fma(fma(fma(fma(__ldg(c + 10), T, __ldg(c + 9)), T, __ldg(c + 8)), T, __ldg(c + 7)), T,
                                   __ldg(c + 6));
             rhocv = fma(xs, cv, rhocv);
+            sm.hRT[s] = hRT;
+            sm.es[s] = es;
         }
     }
     if (f32 && sl == 0) {
@@ -429,7 +446,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         rhocvf = Grp<G>::sum(rhocvf);
         dTdef = __frcp_rn(rhocvf);
         dTde = f2d_alu(dTdef);
-        for (int s = sl; s < ns; s += G) sm.dTdr[s] = (JT)(-d2f_rz(sm.es[s]) * dTdef);
+        // dT/drho_k = -e_k^sens dT/de is formed where the Jacobian needs it
     } else {
         rhocv = Grp<G>::sum(rhocv);
         dTde = frcp(rhocv);
@@ -461,7 +478,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             for (int e = e0; e < e1; ++e) CM += __ldg(m.eff_c + e) * sm.c[__ldg(m.eff_sp + e)];
         }
         const double fwd = kf * Pf, rev = kb * Pb, q = fwd - rev;
-        sm.Q[r] = CM * q;
+        sm.Q[r] = CM * q;   // in the D region until phase 4
         if (f32) {
             // Jacobian-only quantities in FP32 from FP32 copies
             const float* rf = m.rxn_df + (size_t)r * kRxnDStride;
@@ -511,8 +528,9 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
                 if (r < m.ntb) squ += nuj * sm.qtb[r];
             }
         }
-        sm.part[3 * it] = sq;
-        JT *pj = reinterpret_cast<JT *>(sm.part + 3 * it + 1);
+        constexpr int iw = (int)(item_bytes((int)sizeof(JT)) / 8);   // doubles per item
+        sm.part[iw * it] = sq;
+        JT *pj = reinterpret_cast<JT *>(sm.part + iw * it + 1);
         pj[0] = sdq;
         pj[1] = squ;
     }
@@ -523,9 +541,10 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         double sq = 0.0;
         JT sdq = 0, squ = 0;
         const int i0 = __ldg(m.sp_item_ptr + s), i1 = __ldg(m.sp_item_ptr + s + 1);
+        constexpr int iw = (int)(item_bytes((int)sizeof(JT)) / 8);
         for (int it = i0; it < i1; ++it) {
-            sq += sm.part[3 * it];
-            const JT *pj = reinterpret_cast<const JT *>(sm.part + 3 * it + 1);
+            sq += sm.part[iw * it];
+            const JT *pj = reinterpret_cast<const JT *>(sm.part + iw * it + 1);
             sdq += pj[0];
             squ += pj[1];
         }
@@ -534,7 +553,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const JT MJ = f32 ? (JT)__ldg(m.spf + s * kSpStride) : (JT)M;
         const JT efJ = f32 ? (JT)__ldg(m.spf + s * kSpStride + 3) : (JT)ef;
         const double wds = M * sq;
-        sm.wd[s] = wds;
+        // right-hand side -F_s = -(x_s - x0_s - h wdot_s), FP64 until stored
+        sm.rhs[s] = to_jt<JT>(-(sm.x[s] - sm.x0[s] - h * wds));
         const JT ws = MJ * sdq, us = MJ * squ;
         sm.w[s] = ws;
         sm.u[s] = us;
@@ -543,6 +563,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         Ue += efJ * us;
     }
     wde = Grp<G>::sum(wde);
+    if (sl == 0) sm.rhs[ns] = to_jt<JT>(-(sm.x[ns] - sm.x0[ns] - h * wde));
     if (!f32) {
         // the energy row's rank-one parts: J_ek = -sum_s e_f,s J_sk
         We = Grp<G>::sum(We);
@@ -609,11 +630,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     __syncwarp();
     // the per-reaction arrays are dead from here on; the matrix takes their place
 
-    // 5. right-hand side -F = -(x - x0 - h Omega(x))
-    for (int i = sl; i < n; i += G) {
-        const double om = i < ns ? sm.wd[i] : wde;
-        sm.A[i * lda + n] = to_jt<JT>(-(sm.x[i] - sm.x0[i] - h * om));
-    }
+    // 5. right-hand side -F = -(x - x0 - h Omega(x)) into the matrix
+    for (int i = sl; i < n; i += G) sm.A[i * lda + n] = sm.rhs[i];
 
     // 6. species and energy rows of -h J, density columns (longest gather
     //    lists first, so the lanes of a pass run lists of nearly equal
@@ -626,7 +644,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const int len = meta.y >> 16;
         const int s = (meta.y >> 8) & 0xff, k = meta.y & 0xff;
         const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
-        JT J = sm.w[s] * sm.dTdr[k] + sm.u[s] * invMk;
+        const JT dTdrk = f32 ? -sm.esJ[k] * (JT)dTdef : sm.dTdr[k];
+        JT J = sm.w[s] * dTdrk + sm.u[s] * invMk;
         JT a0 = 0, a1 = 0;
         int e = meta.x, q = 0;
         if (f32) {
@@ -766,7 +785,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     //    (the FP32 path takes the norm's ratios in FP32: they decide
     //    convergence, not the iterate)
     double nrm = 0.0, des = 0.0;
-    float nrmf = 0.f;
+    float nrmf = 0.f, desf = 0.f;
     int nonfinite = 0;
     const float escf = f32 ? d2f_rz(escale) : 0.f;
     for (int i = sl; i < n; i += G) {
@@ -779,7 +798,10 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         } else {
             d = (double)sm.A[i * lda + n];
         }
-        des += i < ns ? -sm.es[i] * d : d;
+        if (f32)
+            desf += i < ns ? -(float)sm.esJ[i] * df : df;
+        else
+            des += i < ns ? -sm.es[i] * d : d;
         const double xi = sm.x[i] + d;
         sm.x[i] = xi;
         if (!finite_bits(xi)) nonfinite = 1;
@@ -800,15 +822,20 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     else
         nrm = Grp<G>::max(nrm);
     nonfinite = Grp<G>::any(nonfinite);
-    des = Grp<G>::sum(des);
+    if (f32)
+        des = f2d_alu(Grp<G>::sum(desf));
+    else
+        des = Grp<G>::sum(des);
     __syncwarp();
     norm = nrm;
     bad = sing || nonfinite;
     T_pred = T + des * dTde;
 }
 
+// At most 6 warps per block and 112 registers per thread: 18 warps fit on an
+// SM when shared memory allows it (3 blocks of 6).
 template <int G, typename JT>
-__global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, StepBatch b) {
+__global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, StepOptions o, StepBatch b) {
     extern __shared__ __align__(16) char smem[];
     constexpr int S = 32 / G;
     const int lane = threadIdx.x & 31;
@@ -823,7 +850,7 @@ __global__ void __launch_bounds__(256) be_kernel(DeviceMech m, StepOptions o, St
     // sentinel species: concentration 1, no Gibbs or enthalpy contribution
     if (sl == 0) {
         sm.c[ns] = 1.0;
-        sm.hRT[ns] = 0.0;
+        if (sizeof(JT) == 8) sm.hRT[ns] = 0.0;
         sm.gRT[ns] = 0.0;
     }
     __syncthreads();

@@ -66,7 +66,7 @@ extern "C" int chem_autotune(chem_handle_t hh, int32_t prec, int64_t n_cells, in
     const int nG = small ? 4 : 3;
     int rc = CHEM_OK;
     for (int gi = 0; gi < nG && rc == CHEM_OK; ++gi) {
-        for (int wpb = 1; wpb <= 8; ++wpb) {
+        for (int wpb = 1; wpb <= kMaxBlockThreads / 32; ++wpb) {
             LaunchCfg cfg;
             if (configure(h, prec, Gs[gi], wpb, cfg) != CHEM_OK) continue;   // does not fit
             float ms = 0.f;
