@@ -167,6 +167,15 @@ __device__ __forceinline__ double frcp(double a) {
     e = fma(-a, r, 1.0);
     return fma(r, e, r);
 }
+// One Newton step only (relative error about 1e-14): for reciprocals that
+// scale a convergence ratio or the temperature recovery's Newton step, never
+// a rate, an energy or the elimination.
+__device__ __forceinline__ double frcp1(double a) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+    const double e = fma(-a, r, 1.0);
+    return fma(r, e, r);
+}
 // FP32 reciprocal of the pivot: the hardware approximation (within an ulp or
 // two), enough for an elimination whose result Newton refines in FP64.
 __device__ __forceinline__ float frcp(float a) {
@@ -265,7 +274,7 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
             rfp = f2d_alu(__frcp_rn(fpf));
         } else {
             fp = Grp<G>::sum(fp);
-            rfp = frcp(fp);
+            rfp = frcp1(fp);
         }
         if (!done) {
             const long long fb = __double_as_longlong(f);
@@ -743,6 +752,9 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             }
         }
         __syncwarp();
+        // (the FP64 pivot takes the full-precision reciprocal: a 1e-14 error
+        // in every multiplier reaches the trace species of ill-conditioned
+        // cells at 1e-10)
         const JT inv = frcp(sm.A[j * lda + j]);
         for (int i = j + 1 + sl; i < n; i += G) sm.A[i * lda + j] *= inv;
         __syncwarp();
@@ -813,7 +825,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             const float ri = denf > 0.f ? adf * __frcp_rn(denf) : (adf != 0.f ? CUDART_INF_F : 0.f);
             nrmf = fmaxf(nrmf, ri);
         } else {
-            const double ri = den > 0.0 ? fabs(d) * frcp(den) : (d != 0.0 ? CUDART_INF : 0.0);
+            const double ri = den > 0.0 ? fabs(d) * frcp1(den) : (d != 0.0 ? CUDART_INF : 0.0);
             nrm = fmax(nrm, ri);
         }
     }
