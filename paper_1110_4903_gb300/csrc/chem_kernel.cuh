@@ -491,7 +491,10 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         if (f32) {
             // Jacobian-only quantities in FP32 from FP32 copies
             const float* rf = m.rxn_df + (size_t)r * kRxnDStride;
-            const JT A1v = to_jt<JT>(CM * kf), A2v = to_jt<JT>(CM * kb);
+            // (products formed in FP32 from converted factors: the FP64
+            // pipe keeps to the rates the residual needs)
+            const JT CMf = to_jt<JT>(CM);
+            const JT A1v = CMf * to_jt<JT>(kf), A2v = CMf * to_jt<JT>(kb);
             sm.A1[r] = A1v;
             sm.A2[r] = A2v;
             if (r < m.ntb) sm.qtb[r] = to_jt<JT>(q);

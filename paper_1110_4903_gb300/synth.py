@@ -313,6 +313,13 @@ def hydrocarbon_36sp(seed: int = 36308) -> Mechanism:
     """36 species / 308 reversible reactions over H, O, N, C: 40 third-body
     recombinations A + B + M = AB + M, 12 pressure-independent unimolecular
     decompositions AB = A + B, 256 bimolecular exchanges A + B = C + D."""
+    return hydrocarbon_mechanism(36, 40, 12, 256, seed, "hc-36sp-308r")
+
+
+def hydrocarbon_mechanism(ns: int, n_tb: int, n_uni: int, n_ex: int, seed: int, name: str) -> Mechanism:
+    """ns species over H, O, N, C grown from atoms and diatomics (at most 6
+    atoms), with n_tb third-body recombinations, n_uni pressure-independent
+    unimolecular decompositions and n_ex bimolecular exchanges."""
     rng = np.random.default_rng(seed)
     elements = ["H", "O", "N", "C"]
     comps = [{"H": 1}, {"O": 1}, {"N": 1}, {"C": 1}, {"H": 2}, {"O": 2}, {"N": 2}]
@@ -320,7 +327,7 @@ def hydrocarbon_36sp(seed: int = 36308) -> Mechanism:
     # grow the species set by joining an existing species with an atom or a
     # diatomic (<= 6 atoms), so that every new species has at least one
     # recombination channel; no homonuclear species beyond diatomics
-    while len(comps) < 36:
+    while len(comps) < ns:
         i = int(rng.integers(0, len(comps)))
         j = 0 if rng.uniform() < 0.5 else int(rng.integers(0, 7))
         v = tuple(a + b for a, b in zip(_vec(comps[i], elements), _vec(comps[j], elements)))
@@ -341,19 +348,19 @@ def hydrocarbon_36sp(seed: int = 36308) -> Mechanism:
                 if ab not in (a, b) and np.array_equal(vecs[ab], v):
                     recomb.append(((a, b), (ab,)))
     recomb.sort()
-    if len(recomb) < 52:
+    if len(recomb) < n_tb + n_uni:
         raise RuntimeError("species draw leaves too few recombination channels")
-    pick = rng.choice(len(recomb), size=52, replace=False)
-    tb_set = [recomb[i] for i in pick[:40]]
-    uni_set = [recomb[i] for i in pick[40:]]
+    pick = rng.choice(len(recomb), size=n_tb + n_uni, replace=False)
+    tb_set = [recomb[i] for i in pick[:n_tb]]
+    uni_set = [recomb[i] for i in pick[n_tb:]]
     reactions = [(re, pr, 1) for re, pr in tb_set]
     reactions += [(pr, re, 0) for re, pr in uni_set]
     used = {frozenset([tuple(sorted(re)), tuple(sorted(pr))]) for re, pr, _ in reactions}
     ex = _balanced_pairs(names, comp_map, elements, (2,), (2,), exclude=used)
     ex.sort()
-    if len(ex) < 256:
+    if len(ex) < n_ex:
         raise RuntimeError("species draw leaves too few exchange channels")
-    pick = rng.choice(len(ex), size=256, replace=False)
+    pick = rng.choice(len(ex), size=n_ex, replace=False)
     for i in sorted(pick):
         reactions.append((ex[i][0], ex[i][1], 0))
     nasa = _species_thermo(rng, [(n, comp_map[n]) for n in names])
@@ -361,7 +368,7 @@ def hydrocarbon_36sp(seed: int = 36308) -> Mechanism:
     reactions = _orient(reactions, nasa, index)
     A, beta, Ea = _arrhenius(rng, len(reactions))
     eff = _efficiencies(rng, reactions, len(names))
-    return make_mechanism("hc-36sp-308r", names, comp_map, elements, reactions, nasa,
+    return make_mechanism(name, names, comp_map, elements, reactions, nasa,
                           A, beta, Ea, tb_eff=eff)
 
 

@@ -206,3 +206,32 @@ def test_point_implicit_mode(torch, wl, ncell, dt):
     assert (og["newton_iters"][oo["status"] == 0] == 1).all()
     P.compare(rg, eg, og, rr, er, oo, rho, P.TOL_FP64, min_same=1.0)
     c.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_maximum_species_count(torch, precision):
+    """The largest mechanism the library takes: 64 species (65 x 65 systems,
+    so every per-unknown loop runs three passes at 32 lanes per cell), 480
+    reactions, against the oracle."""
+    from paper_1110_4903_gb300 import chem
+    m = synth.hydrocarbon_mechanism(64, 60, 20, 400, 64480, "hc-64sp-480r")
+    f = synth.uniform_field(m.ns, 64, 900.0, 2800.0, seed=64)
+    rho, e = P.initial_state(m, f)
+    dt = 1e-6
+    if precision == "fp64":
+        c = chem.Chem(m)
+        assert c.lanes(chem.FP64) == 32
+        rr, er, oo = P.oracle_reference(m, rho, e, dt, f.T, threads=THREADS)
+        rg, eg, og = P.gpu_run(torch, c, rho, e, dt, T_in=f.T)
+        P.compare(rg, eg, og, rr, er, oo, rho, P.TOL_FP64, min_same=0.9, flip_tol=1e-3)
+    else:
+        c = chem.Chem(m, precision=chem.MIXED)
+        rr, er, oo = P.oracle_reference(m, rho, e, dt, f.T, threads=THREADS, **P.MIXED_OPTS)
+        rg, eg, og = P.gpu_run(torch, c, rho, e, dt, T_in=f.T)
+        ok = oo["status"] == 0
+        assert np.array_equal(og["status"], oo["status"]) and ok.mean() >= 0.95
+        same = ok & (og["substeps"] == oo["substeps"]) & (og["failures"] == oo["failures"])
+        rel = np.abs(rg - rr) / np.maximum(np.abs(rr), 1e-9 * rho.sum(0)[None, :])
+        assert same.mean() >= 0.85
+        assert rel[:, same].max() <= P.TOL_MIXED
+    c.close()
