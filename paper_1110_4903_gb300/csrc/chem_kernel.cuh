@@ -300,15 +300,16 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
     if (need) T_out = T;
 }
 
-// Trailing update a_ik -= l_ij a_jk of elimination step j (i > j, k > j,
-// the augmented column included), organised by columns: a lane owns a column,
-// keeps a_jk in a register and walks the rows four at a time, so four
-// independent updates are in flight and the multipliers l_ij are broadcast
+// Trailing update a_ik -= a_ij (a_jk / a_jj) of elimination step j (i > j,
+// k > j, the augmented column included), organised by columns: a lane owns a
+// column, keeps a_jk / a_jj in a register and walks the rows four at a time,
+// so four independent updates are in flight and the a_ij are broadcast
 // reads.  When fewer columns than lanes remain, the rows of each column are
-// split over 2, 4, ... lanes.  Every element still receives one fused
-// multiply-add per step, in the same order of steps as the element-wise walk.
+// split over 2, 4, ... lanes.  The multipliers are never stored: the
+// right-hand side is eliminated with the matrix, and back substitution reads
+// U only.
 template <int G, typename JT>
-__device__ __forceinline__ void lu_update_by_columns(JT *A, int lda, int n, int j, int sl) {
+__device__ __forceinline__ void lu_update_by_columns(JT *A, int lda, int n, int j, int sl, JT inv) {
     const int C = n - j, R = n - j - 1;
     if (R <= 0) return;
     int kc = sl, i0 = j + 1, i1 = n;
@@ -323,7 +324,7 @@ __device__ __forceinline__ void lu_update_by_columns(JT *A, int lda, int n, int 
     }
     const JT *cj = A + j;
     for (int k = j + 1 + kc; k <= n; k += G) {
-        const JT ajk = A[j * lda + k];
+        const JT ajk = A[j * lda + k] * inv;
         JT *ck = A + k;
         int i = i0;
         for (; i + 4 <= i1; i += 4) {
@@ -759,12 +760,15 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         // in every multiplier reaches the trace species of ill-conditioned
         // cells at 1e-10)
         const JT inv = frcp(sm.A[j * lda + j]);
-        for (int i = j + 1 + sl; i < n; i += G) sm.A[i * lda + j] *= inv;
-        __syncwarp();
-        if (sl == 0) sm.A[j * lda + j] = inv;
+        if (!f32) {
+            for (int i = j + 1 + sl; i < n; i += G) sm.A[i * lda + j] *= inv;
+            __syncwarp();
+            if (sl == 0) sm.A[j * lda + j] = inv;
+        }
         if (f32) {
-            // FP32: bound by issue and latency, not by the pipe
-            lu_update_by_columns<G, JT>(sm.A, lda, n, j, sl);
+            // FP32: bound by issue and latency, not by the pipe; the update
+            // reads column j unscaled and never A[j][j]
+            lu_update_by_columns<G, JT>(sm.A, lda, n, j, sl, inv);
         } else {
             // FP64: a flat walk over the trailing elements keeps every lane of
             // every FP64 instruction busy (a masked lane costs a full slot)
@@ -784,7 +788,10 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             }
         }
         __syncwarp();
+        // FP32: the reciprocal replaces the pivot once every lane has read it
+        if (f32 && sl == 0) sm.A[j * lda + j] = inv;
     }
+    __syncwarp();
     // back substitution, U delta = y
     for (int j = n - 1; j >= 0; --j) {
         const JT dj = sm.A[j * lda + n] * sm.A[j * lda + j];
