@@ -32,6 +32,12 @@ WORKLOAD_DESC = ("synthetic 36 sp / 308 rxn mechanism (4 elements, 40 third-body
                  "Dirichlet(1) mass fractions, one dt = 1e-6 s backward-Euler chemistry step with "
                  "adaptive substeps")
 EXP_FLOPS = 40          # one FP64 exp occupies the FP64 pipe like ~20 DFMA (measured)
+# DRAM bytes (read + write) of one launch of the step kernel on the default
+# workload (2^18 cells, state and tables cold after the L2 flush), from a
+# single-pass ncu capture of a full-size launch of the current kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum; part of the state written
+# back is still in L2 when the kernel ends).  Other workloads report null.
+MEASURED_TRAFFIC = {"mixed": 80.11e6 + 30.51e6, "fp64": 80.23e6 + 37.60e6}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 x max clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FFMA/clk x 2 x max clock
 
@@ -445,8 +451,11 @@ def main():
             a64 = it * wm["mixed_fp64"] / (kern_ms * 1e-3) / 1e12
             a32 = it * wm["mixed_fp32"] / (kern_ms * 1e-3) / 1e12
         bytes_launch = n * (16 * (mech.ns + 1) + 8)
+        full_default = args.workload == WORKLOAD and not args.cells
         roof = {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": a64 / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": a64 / FP64_PEAK_TFLOPS,
+                "traffic": MEASURED_TRAFFIC[name] if full_default else None,
+                "traffic_unit": "bytes per launch (DRAM read + write)",
                 "kernel": "chem::be_kernel<%d,%s>" % (ch.lanes(prec), "double" if name == "fp64" else "float"),
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe, the "
                                "binding pipe); probe measured 1.193 TFLOP/s",
