@@ -165,6 +165,7 @@ static void third_body_first(const chem_mech_desc *in, ReorderedMech &o) {
 // Derived tables (layouts in chem_internal.h)
 struct HostTables {
     std::vector<double> thermo, tmid, tpoly, sp, rxn_d, eff_c, d_c, j_c, sp_nu, exp_tab;
+    std::vector<unsigned> div16;
     std::vector<float> tpoly_f;
     std::vector<float> rxn_df, d_cef, spf;
     std::vector<int4> d_pk;
@@ -392,6 +393,9 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     }
     t.n_items = (int)t.it_ptr.size() - 1;
     // 2^(j/256), from the exponential of the exact arguments in long double
+    // reciprocals for the elimination's small divisions (numerators below 64)
+    t.div16.assign(67, 0u);
+    for (int c = 1; c <= 66; ++c) t.div16[c] = (65536u + c - 1) / c;
     t.exp_tab.resize(kExpTab);
     for (int j = 0; j < kExpTab; ++j) t.exp_tab[j] = (double)std::exp2l((long double)j / kExpTab);
     // FP32 copies for the mixed-precision Jacobian
@@ -486,7 +490,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
                  i_sp = addv(t.sp), i_rd = addv(t.rxn_d),
                  i_rf = addv(t.rxn_f), i_ep = addv(t.eff_ptr), i_es = addv(t.eff_sp), i_ec = addv(t.eff_c),
                  i_dpk = addv(t.d_pk), i_dc = addv(t.d_c), i_sip = addv(t.sp_item_ptr),
-                 i_ex = addv(t.exp_tab), i_rdf = addv(t.rxn_df), i_dcef = addv(t.d_cef),
+                 i_ex = addv(t.exp_tab), i_div = addv(t.div16), i_rdf = addv(t.rxn_df), i_dcef = addv(t.d_cef),
                  i_spf = addv(t.spf);
     size_t i_lay[kLayouts][8];
     for (int li = 0; li < kLayouts; ++li) {
@@ -545,6 +549,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     m.sp_item_ptr = (const int *)at(i_sip);
 
     m.exp_tab = (const double *)at(i_ex);
+    m.div16 = (const unsigned *)at(i_div);
     m.rxn_df = (const float *)at(i_rdf);
     m.d_cef = (const float *)at(i_dcef);
 

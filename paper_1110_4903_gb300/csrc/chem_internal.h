@@ -124,6 +124,7 @@ struct DeviceMech {
     GatherLayout gl[kLayouts];
     const int *sp_item_ptr;     // [ns+1] work items of each species
     const double *exp_tab;      // [kExpTab] 2^(j/kExpTab)
+    const unsigned *div16;      // [67] ceil(2^16 / c): x / c = (x div16[c]) >> 16 for x < 64
     // FP32 copies for the mixed-precision Jacobian
     const float *rxn_df;        // [nr][4] beta, Ea/R, sum nu, 0
     const float *d_cef;         // [nD] efficiency coefficient in FP32

@@ -772,11 +772,16 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         } else {
             // FP64: a flat walk over the trailing elements keeps every lane of
             // every FP64 instruction busy (a masked lane costs a full slot)
+            // (sl / cols and G / cols by a reciprocal multiply: both numerators
+            // are below 64, and an integer division would take conversions on
+            // the FP64 pipe)
             const int cols = n - j;
             const int tot = (n - j - 1) * cols;
+            const unsigned rc = __ldg(m.div16 + cols);
             int e = sl;
-            int i = j + 1 + e / cols, k = j + 1 + e % cols;
-            const int di = G / cols, dk = G % cols;
+            const int q0 = (int)(((unsigned)sl * rc) >> 16), dq = (int)(((unsigned)G * rc) >> 16);
+            int i = j + 1 + q0, k = j + 1 + (sl - q0 * cols);
+            const int di = dq, dk = G - dq * cols;
             for (; e < tot; e += G) {
                 sm.A[i * lda + k] -= sm.A[i * lda + j] * sm.A[j * lda + k];
                 i += di;

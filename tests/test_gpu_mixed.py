@@ -52,3 +52,26 @@ def test_mixed_against_oracle(torch, wl, ncell, opts):
     assert st["max_rel_same"] <= P.TOL_MIXED and st["max_relT_same"] <= P.TOL_MIXED
     assert st["frac_same"] >= 0.9
     c.close()
+
+
+@pytest.mark.parametrize("wl,ncell,lanes", [("h2air-1M", 1000, 2), ("h2air-1M", 1000, 4), ("h2air-1M", 1000, 8),
+                                            ("h2air-1M", 1000, 16), ("h2air-1M", 1000, 32),
+                                            ("hc36-256k", 64, 8), ("hc36-256k", 64, 16)])
+def test_mixed_every_lane_width(torch, wl, ncell, lanes):
+    # every FP32 kernel instantiation against the oracle under the same
+    # Newton control: the elimination's row splits (fewer columns than lanes),
+    # the per-lane-count gather layouts and the shuffle argmax of G < 32
+    from paper_1110_4903_gb300 import chem
+    m, f, dt = synth.workload(wl)
+    idx = np.arange(ncell) * 997 % f.n
+    fs = synth.subsample(f, idx)
+    rho, e = P.initial_state(m, fs)
+    c = chem.Chem(m, precision=chem.MIXED, lanes_per_cell=lanes)
+    assert c.lanes(chem.MIXED) == lanes
+    rr, er, oo = P.oracle_reference(m, rho, e, dt, fs.T, threads=THREADS, **P.MIXED_OPTS)
+    rg, eg, og = P.gpu_run(torch, c, rho, e, dt, T_in=fs.T, ld=ncell + 3)
+    st = _stats(rg, eg, og, rr, er, oo, rho)
+    assert st["status_equal"] == 1.0
+    assert st["max_rel_same"] <= P.TOL_MIXED and st["max_relT_same"] <= P.TOL_MIXED
+    assert st["frac_same"] >= 0.85
+    c.close()
