@@ -41,7 +41,23 @@ extern "C" int chem_autotune(chem_handle_t hh, int32_t prec, int64_t n_cells, in
     if (ld == 0) ld = n_cells;
     if (ld < n_cells || !(dt >= 0)) return fail(CHEM_E_INVALID_ARG, "sizes or dt");
     const int ns = h->ns;
-    const long long m = n_cells < 16384 ? n_cells : 16384;
+    const int Gs_small[] = {2, 4, 8, 16};
+    const int Gs_large[] = {8, 16, 32};
+    const bool small = ns + 1 <= 16;
+    const int *Gs = small ? Gs_small : Gs_large;
+    const int nG = small ? 4 : 3;
+    // the sample fills the GPU with at least eight waves of the candidate that
+    // holds the most cells at once (a sample smaller than a wave times the
+    // slowest cell, not the throughput)
+    long long wave = 0;
+    for (int gi = 0; gi < nG; ++gi) {
+        LaunchCfg cfg;
+        if (configure(h, prec, Gs[gi], 0, cfg) != CHEM_OK) continue;
+        const long long cells = (long long)cfg.grid * (cfg.block / 32) * (32 / Gs[gi]);
+        if (cells > wave) wave = cells;
+    }
+    long long m = 8 * wave > 16384 ? 8 * wave : 16384;
+    if (m > n_cells) m = n_cells;
     const long long stride = n_cells / m;
     cudaStream_t st = (cudaStream_t)stream;
     // pristine sample, work copy, temperature guesses
@@ -59,11 +75,6 @@ extern "C" int chem_autotune(chem_handle_t hh, int32_t prec, int64_t n_cells, in
     cudaEventCreate(&e1);
     int best_G = 0, best_w = 0;
     float best_ms = 1e30f;
-    const int Gs_small[] = {2, 4, 8, 16};
-    const int Gs_large[] = {8, 16, 32};
-    const bool small = ns + 1 <= 16;
-    const int *Gs = small ? Gs_small : Gs_large;
-    const int nG = small ? 4 : 3;
     int rc = CHEM_OK;
     for (int gi = 0; gi < nG && rc == CHEM_OK; ++gi) {
         for (int wpb = 1; wpb <= kMaxBlockThreads / 32; ++wpb) {

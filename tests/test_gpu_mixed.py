@@ -75,3 +75,49 @@ def test_mixed_every_lane_width(torch, wl, ncell, lanes):
     assert st["max_rel_same"] <= P.TOL_MIXED and st["max_relT_same"] <= P.TOL_MIXED
     assert st["frac_same"] >= 0.85
     c.close()
+
+
+@pytest.mark.parametrize("wl,sample", [("hc36-256k", 96), ("hc36-front-2M", 96)])
+def test_mixed_full_size_sampled(torch, wl, sample):
+    """The benchmark's headline path at full size in its launch configuration:
+    every cell conserves mass and energy, a random sample matches the oracle
+    under the same Newton control."""
+    from paper_1110_4903_gb300 import chem
+    m, f, dt = synth.workload(wl)
+    c = chem.Chem(m, precision=chem.MIXED)
+    dev = torch.device("cuda")
+    T = torch.tensor(f.T, device=dev)
+    Y = torch.tensor(f.Y, device=dev)
+    rho = torch.zeros_like(Y)
+    e = torch.zeros_like(T)
+    c.state_from_tpy(T, torch.tensor(f.P, device=dev), Y, rho, e)
+    rho0, e0 = rho.clone(), e.clone()
+    n = f.n
+    T_out = torch.zeros_like(T)
+    outs = [torch.zeros(n, dtype=torch.int32, device=dev) for _ in range(4)]
+    c.advance(rho, e, dt, T_in=T, T_out=T_out, status=outs[0], newton_iters=outs[1], substeps=outs[2],
+              failures=outs[3])
+    torch.cuda.synchronize()
+    ef = torch.tensor(P.oracle.OracleMech(m).ef(), device=dev)
+    st, it, su, fa = (t.cpu().numpy() for t in outs)
+    # conservation: BE conserves mass and U = e + sum e_f rho exactly at its
+    # root; the mixed path stops an accepted substep up to kappa x tolerance
+    # away from the root (contraction-rate stop), so each accepted substep may
+    # leave kappa (rtol + ns atol_rel) of relative mass or energy, carried on
+    bound = 1e-13 + torch.tensor(su, device=dev, dtype=torch.float64) * P.MIXED_OPTS["conv_kappa"] * (
+        1e-10 + m.ns * 1e-12)
+    assert (((rho.sum(0) - rho0.sum(0)).abs() / rho0.sum(0)) <= bound).all()
+    U0, U1 = e0 + ef @ rho0, e + ef @ rho
+    assert (((U1 - U0).abs() / (e0.abs() + ef.abs() @ rho0.abs())) <= bound).all()
+    assert (st == 0).mean() >= 0.9999
+    rng = np.random.default_rng(321)
+    idx = np.sort(rng.choice(n, sample, replace=False))
+    r0, e0s = rho0[:, idx].cpu().numpy(), e0[idx].cpu().numpy()
+    rr, er, oo = P.oracle_reference(m, r0, e0s, dt, f.T[idx], threads=THREADS, **P.MIXED_OPTS)
+    og = dict(T=T_out[idx].cpu().numpy(), status=st[idx], newton_iters=it[idx], substeps=su[idx],
+              failures=fa[idx])
+    s = _stats(rho[:, idx].cpu().numpy(), e[idx].cpu().numpy(), og, rr, er, oo, r0)
+    assert s["status_equal"] == 1.0
+    assert s["max_rel_same"] <= P.TOL_MIXED and s["max_relT_same"] <= P.TOL_MIXED
+    assert s["frac_same"] >= 0.85
+    c.close()
