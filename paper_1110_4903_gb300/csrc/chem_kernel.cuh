@@ -157,15 +157,14 @@ __device__ __forceinline__ bool key_is_inf(unsigned long long k, float) {
     return k >= ((unsigned long long)0x7f800000u << 29);
 }
 
-// Reciprocal: hardware approximation refined by two Newton steps
-// (r <- r + r (1 - a r)), each doubling the correct bits.
+// Reciprocal: the hardware approximation r refined with its residual
+// e = 1 - a r as r (1 + e + e^2), whose error is e^3 (the approximation is
+// good to about 2^-23, so below FP64 rounding): three FP64 operations.
 __device__ __forceinline__ double frcp(double a) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
-    double e = fma(-a, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-a, r, 1.0);
-    return fma(r, e, r);
+    const double e = fma(-a, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 // One Newton step only (relative error about 1e-14): for reciprocals that
 // scale a convergence ratio or the temperature recovery's Newton step, never
