@@ -93,7 +93,7 @@ typedef struct chem_options {
     int32_t max_attempts;     /* substep attempts per cell, 1..1e6              */
     int32_t point_implicit;   /* 1: one linearised step per substep (Eq. 29 as printed) */
     int32_t div_check;        /* 1: abandon a substep whose Newton norm stops falling */
-    int32_t lanes_per_cell;   /* 0 = chosen by the library; else 1,2,4,8,16,32 */
+    int32_t lanes_per_cell;   /* 0 = chosen by the library; else 2, 4, 8, 16 or 32 */
     int32_t autotune;         /* 1: time the lane choices once and keep the best */
     int64_t hbm_budget_bytes; /* serving: device bytes requests may hold (0 = 50% of free) */
     int32_t max_newton_mixed; /* Newton iterations per attempt on the CHEM_MIXED path, whose

@@ -8,14 +8,22 @@
 // rates, the Jacobian and its LU live in shared memory; HBM only sees the
 // cell state (SoA) on load and store.
 //
-// FP64 is the binding pipe on this part (2 DFMA/clk/SM against 128 FFMA), so
-// the iteration is laid out to keep every FP64 warp instruction full: each
-// phase is one loop over a flat, uniform work list (reactions, D entries,
-// Jacobian entries ordered by gather length, fixed-size chunks of the
-// species lists), coefficients are stored as doubles (no int-to-double
-// conversions), the pivot search compares integer keys, reciprocals come
-// from rcp.approx plus Newton steps, and exp is a short table-driven
-// evaluation.
+// FP64 is the binding pipe on this part: 2 DFMA/clk/SM against 128 FFMA, and a
+// partly masked FP64 instruction or an FP64<->FP32 conversion costs a full
+// FP64 slot.  So:
+//   - each phase is one loop over a flat, uniform work list (reactions, D
+//     entries, Jacobian entries ordered by gather length and interleaved by
+//     pass, fixed-size chunks of the species lists);
+//   - coefficients are stored in the type they are used in, and the mixed
+//     path converts between FP64 and FP32 on the integer pipe;
+//   - pivot searches, range choices and finiteness tests compare integer
+//     keys; reciprocals refine rcp.approx; exp is a short table-driven
+//     evaluation, and the temperature recovery a multiplied-out polynomial.
+// The mixed path (JT = float) keeps the FP64 residual, rates, sources and
+// temperature, and moves everything that only feeds the Jacobian to FP32;
+// its LU is organised by columns, and its energy row is formed from the
+// species rows.  It is bound by latency, so its slot layout is cut to what
+// it reads (18 warps per SM at 36 species).
 #pragma once
 
 #include <cuda_runtime.h>
