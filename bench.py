@@ -426,8 +426,9 @@ def main():
     wall = 0.0
     for name, ch in handles.items():
         prec = chem.MIXED if name == "mixed" else chem.FP64
+        shape = None
         if args.autotune:
-            ch.autotune(rho0, e0, dt, T_in=T, precision=prec, stream=stream)
+            shape = ch.autotune(rho0, e0, dt, T_in=T, precision=prec, stream=stream)
         # untimed statistics launch: Newton iterations for the work model
         _, _, stats = time_path(torch, ch, rho0, e0, T, dt, prec, 1, 0, flush, stream, True)
         launches0 = ch.launch_count()
@@ -473,6 +474,8 @@ def main():
                              newton_iters_mean=stats["newton_iters_mean"],
                              newton_iters_max=stats["newton_iters_max"],
                              cells_ok=stats["status_ok"], roofline=roof)
+        if shape is not None:
+            results[name]["autotuned_warps_per_block"] = shape[1]
         if args.workload != WORKLOAD:
             # Newton iterations per cell: histogram over 0..63, 64 = 64 or more
             results[name]["newton_iters_hist"] = stats["newton_iters_hist"]

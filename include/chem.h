@@ -198,11 +198,14 @@ int chem_temperature(chem_handle_t h, int64_t n_cells, int64_t ld, const double 
 
 /* Autotuner: times every launch shape the shared memory allows -- lanes per
  * cell (cells per warp = 32/lanes) and warps per block -- on a strided
- * sample of the given cells large enough for eight waves of the shape that
- * holds the most cells (at least 16,384 cells, at most all of them; device
- * buffers, same layout as chem_advance_ex; the cells themselves are not
- * modified: the sample is copied), keeps the fastest for `precision` on this
- * handle and returns it.
+ * sample of the given cells (device buffers, same layout as
+ * chem_advance_ex; the cells themselves are not modified: the sample is
+ * copied), keeps the fastest for `precision` on this handle and returns it.
+ * The sample starts at eight waves of the shape that holds the most cells
+ * (at least 16,384 cells) and grows, up to all of the cells, until one step
+ * of it in the default shape takes 100 ms: where work per cell varies
+ * widely, a short sample would time its hardest cells' latency instead of
+ * the throughput.
  * Synchronous.  With chem_options.autotune = 1 the first chem_advance_ex of
  * each precision runs it on its own cells first. */
 int chem_autotune(chem_handle_t h, int32_t precision, int64_t n_cells, int64_t ld,

@@ -9,6 +9,9 @@
 
 namespace chem {
 
+// A sample is grown until one step of it takes this long in the default shape.
+constexpr float kTuneTargetMs = 100.f;
+
 // Gathers a strided sample of cells into contiguous buffers.
 __global__ void gather_cells_kernel(int ns, long long m, long long stride, long long ld, const double *rho,
                                     const double *e, const double *T, double *rho_o, double *e_o,
@@ -58,48 +61,78 @@ extern "C" int chem_autotune(chem_handle_t hh, int32_t prec, int64_t n_cells, in
     }
     long long m = 8 * wave > 16384 ? 8 * wave : 16384;
     if (m > n_cells) m = n_cells;
-    const long long stride = n_cells / m;
     cudaStream_t st = (cudaStream_t)stream;
     // pristine sample, work copy, temperature guesses
-    double *buf = nullptr;
-    const size_t per = (size_t)m * (ns + 1);
-    cudaError_t ce = cudaMalloc(&buf, sizeof(double) * (2 * per + m));
-    if (ce != cudaSuccess) return fail(CHEM_E_OOM, "autotune sample buffers");
-    double *s_rho = buf, *s_e = buf + (size_t)m * ns, *w_rho = buf + per, *w_e = w_rho + (size_t)m * ns,
-           *s_T = buf + 2 * per;
-    gather_cells_kernel<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(ns, m, stride, ld, rho_s, e, T_in, s_rho, s_e,
-                                                                    s_T);
-    h->launches.fetch_add(1);
+    double *buf = nullptr, *s_rho = nullptr, *s_e = nullptr, *w_rho = nullptr, *w_e = nullptr, *s_T = nullptr;
+    size_t per = 0;
+    auto take_sample = [&](long long mm) -> int {
+        if (buf) cudaFree(buf);
+        buf = nullptr;
+        per = (size_t)mm * (ns + 1);
+        const cudaError_t ce = cudaMalloc(&buf, sizeof(double) * (2 * per + mm));
+        if (ce != cudaSuccess) return fail(CHEM_E_OOM, "autotune sample buffers");
+        s_rho = buf;
+        s_e = buf + (size_t)mm * ns;
+        w_rho = buf + per;
+        w_e = w_rho + (size_t)mm * ns;
+        s_T = buf + 2 * per;
+        gather_cells_kernel<<<(unsigned)((mm + 127) / 128), 128, 0, st>>>(ns, mm, n_cells / mm, ld, rho_s, e, T_in,
+                                                                         s_rho, s_e, s_T);
+        h->launches.fetch_add(1);
+        return CHEM_OK;
+    };
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // one step of the sample in shape cfg; the second of two runs is timed
+    auto time_cfg = [&](LaunchCfg &cfg, float &ms) -> int {
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaMemcpyAsync(w_rho, s_rho, sizeof(double) * per, cudaMemcpyDeviceToDevice, st);
+            chem_advance_args a;
+            memset(&a, 0, sizeof a);
+            a.n_cells = m;
+            a.ld = m;
+            a.rho_s = w_rho;
+            a.e = w_e;
+            a.dt = dt;
+            a.T_in = s_T;
+            a.stream = st;
+            cudaEventRecord(e0, st);
+            const int r = launch_cfg(h, &a, prec, &cfg, next_counter(h));
+            cudaEventRecord(e1, st);
+            if (r) return r;
+            const cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) return cuda_fail(ce, "autotune run");
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        return CHEM_OK;
+    };
+    int rc = take_sample(m);
+    // Work per cell can vary by orders of magnitude across a field (a flame
+    // front among cold gas): a sample that runs for less time than its
+    // hardest cells times their latency, not the throughput.  Grow it until
+    // the library's default shape needs kTuneTargetMs on it.
+    {
+        LaunchCfg cfg;
+        for (int grow = 0; rc == CHEM_OK && grow < 4 && m < n_cells; ++grow) {
+            float ms = 0.f;
+            if (configure(h, prec, h->lanes[prec], 0, cfg) != CHEM_OK) break;
+            rc = time_cfg(cfg, ms);
+            if (rc || ms >= kTuneTargetMs) break;
+            const double f = ms > 0.f ? kTuneTargetMs / ms : 64.0;
+            long long mm = (long long)(m * (f < 2.0 ? 2.0 : f > 64.0 ? 64.0 : f));
+            m = mm < n_cells ? mm : n_cells;
+            rc = take_sample(m);
+        }
+    }
     int best_G = 0, best_w = 0;
     float best_ms = 1e30f;
-    int rc = CHEM_OK;
     for (int gi = 0; gi < nG && rc == CHEM_OK; ++gi) {
         for (int wpb = 1; wpb <= kMaxBlockThreads / 32; ++wpb) {
             LaunchCfg cfg;
             if (configure(h, prec, Gs[gi], wpb, cfg) != CHEM_OK) continue;   // does not fit
             float ms = 0.f;
-            for (int rep = 0; rep < 2; ++rep) {
-                cudaMemcpyAsync(w_rho, s_rho, sizeof(double) * per, cudaMemcpyDeviceToDevice, st);
-                chem_advance_args a;
-                memset(&a, 0, sizeof a);
-                a.n_cells = m;
-                a.ld = m;
-                a.rho_s = w_rho;
-                a.e = w_e;
-                a.dt = dt;
-                a.T_in = s_T;
-                a.stream = st;
-                cudaEventRecord(e0, st);
-                rc = launch_cfg(h, &a, prec, &cfg, next_counter(h));
-                cudaEventRecord(e1, st);
-                if (rc) break;
-                ce = cudaEventSynchronize(e1);
-                if (ce != cudaSuccess) { rc = cuda_fail(ce, "autotune run"); break; }
-                cudaEventElapsedTime(&ms, e0, e1);
-            }
+            rc = time_cfg(cfg, ms);
             if (rc) break;
             if (ms < best_ms) {
                 best_ms = ms;
