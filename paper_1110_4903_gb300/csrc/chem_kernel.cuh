@@ -24,6 +24,12 @@
 // its LU is organised by columns, and its energy row is formed from the
 // species rows.  It is bound by latency, so its slot layout is cut to what
 // it reads (18 warps per SM at 36 species).
+//   Code size: with 18 warps at different phases, the instructions of one
+// Newton iteration have to stay in the SM's instruction caches.  The
+// compiler's unrolling of the many short runtime-count loops made the mixed
+// kernel 114 KB, and instruction fetch its first stall; every loop below is
+// therefore kept rolled (#pragma unroll 1) unless it says otherwise, and
+// the few unrolled bodies are written out by hand.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -251,12 +257,14 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
     bool done = !need;
     ok = false;
     const double e = x[ns];
+#pragma unroll 1
     for (int it = 1; it <= kTmaxIter; ++it) {
         if (!__any_sync(kFull, !done)) break;
         const long long Tb = __double_as_longlong(T);
         const float Tf = F32 ? d2f_rz(T) : 0.f;
         double f = 0.0, fp = 0.0;
         float fpf = 0.f;
+#pragma unroll 1
         for (int s = sl; s < ns; s += G) {
             const int row = thermo_range_row(m, s, Tb);
             const double *c = m.tpoly + (size_t)row * kTpolyStride;
@@ -330,10 +338,12 @@ __device__ __forceinline__ void lu_update_by_columns(JT *A, int lda, int n, int 
         i1 = min(n, i0 + rows);
     }
     const JT *cj = A + j;
+#pragma unroll 1
     for (int k = j + 1 + kc; k <= n; k += G) {
         const JT ajk = A[j * lda + k] * inv;
         JT *ck = A + k;
         int i = i0;
+#pragma unroll 1
         for (; i + 4 <= i1; i += 4) {
             const JT l0 = cj[i * lda], l1 = cj[(i + 1) * lda], l2 = cj[(i + 2) * lda], l3 = cj[(i + 3) * lda];
             const JT v0 = ck[i * lda], v1 = ck[(i + 1) * lda], v2 = ck[(i + 2) * lda], v3 = ck[(i + 3) * lda];
@@ -342,6 +352,7 @@ __device__ __forceinline__ void lu_update_by_columns(JT *A, int lda, int n, int 
             ck[(i + 2) * lda] = fma(-l2, ajk, v2);
             ck[(i + 3) * lda] = fma(-l3, ajk, v3);
         }
+#pragma unroll 1
         for (; i < i1; ++i) ck[i * lda] = fma(-cj[i * lda], ajk, ck[i * lda]);
     }
 }
@@ -422,6 +433,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     const float Tf = f32 ? d2f_rz(T) : 0.f;
     double ctot = 0.0, rhocv = 0.0;
     float rhocvf = 0.f;
+#pragma unroll 1
     for (int s = sl; s < ns; s += G) {
         const double *spr = m.sp + s * kSpStride;
         const double xs = sm.x[s];
@@ -467,6 +479,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     } else {
         rhocv = Grp<G>::sum(rhocv);
         dTde = frcp(rhocv);
+#pragma unroll 1
         for (int s = sl; s < ns; s += G) sm.dTdr[s] = (JT)(-sm.es[s] * dTde);
     }
     __syncwarp();
@@ -474,6 +487,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     // 2. rates per reaction: Eq. 23 forward rate, Eq. 24 equilibrium
     //    constant, Eq. 25 progress rate, and their temperature derivatives
     const JT iT = to_jt<JT>(invT);
+#pragma unroll 1
     for (int r = sl; r < nr; r += G) {
         const double *rd = m.rxn_d + (size_t)r * kRxnDStride;
         const double lnA = __ldg(rd + 0), beta = __ldg(rd + 1), EaR = __ldg(rd + 2), dnu = __ldg(rd + 3);
@@ -492,6 +506,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         if (tb) {
             CM = ctot;
             const int e0 = __ldg(m.eff_ptr + r), e1 = __ldg(m.eff_ptr + r + 1);
+#pragma unroll 1
             for (int e = e0; e < e1; ++e) CM += __ldg(m.eff_c + e) * sm.c[__ldg(m.eff_sp + e)];
         }
         const double fwd = kf * Pf, rev = kb * Pb, q = fwd - rev;
@@ -531,6 +546,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     //    (an item's partial sums: sum nu Q in FP64, then sum nu dQ/dT and
     //    sum nu q_tb in the Jacobian type, packed into the next 16 bytes)
     const GatherLayout &gl = m.gl[layout_index(G)];
+#pragma unroll 1
     for (int it = sl; it < m.n_items; it += G) {
         const int2 im = __ldg(gl.it_meta + it);
         double sq = 0.0;
@@ -557,11 +573,13 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     __syncwarp();
     double wde = 0.0;
     JT We = 0, Ue = 0;
+#pragma unroll 1
     for (int s = sl; s < ns; s += G) {
         double sq = 0.0;
         JT sdq = 0, squ = 0;
         const int i0 = __ldg(m.sp_item_ptr + s), i1 = __ldg(m.sp_item_ptr + s + 1);
         constexpr int iw = (int)(item_bytes((int)sizeof(JT)) / 8);
+#pragma unroll 1
         for (int it = i0; it < i1; ++it) {
             sq += sm.part[iw * it];
             const JT *pj = reinterpret_cast<const JT *>(sm.part + iw * it + 1);
@@ -617,6 +635,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             return d;
         };
         int j = sl;
+#pragma unroll 1
         for (; j + G < m.nD; j += 2 * G) {
             const JT d0 = dval(j), d1 = dval(j + G);
             Dw[j] = d0;
@@ -624,6 +643,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         }
         if (j < m.nD) Dw[j] = dval(j);
     } else
+#pragma unroll 1
     for (int j = sl; j < m.nD; j += G) {
         const int2 pk = __ldg(reinterpret_cast<const int2 *>(m.d_pk + j));
         const int i0 = pk.x, i1 = pk.y;
@@ -651,6 +671,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     // the per-reaction arrays are dead from here on; the matrix takes their place
 
     // 5. right-hand side -F = -(x - x0 - h Omega(x)) into the matrix
+#pragma unroll 1
     for (int i = sl; i < n; i += G) sm.A[i * lda + n] = sm.rhs[i];
 
     // 6. species and energy rows of -h J, density columns (longest gather
@@ -659,6 +680,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     //    (four terms in flight per trip, two accumulators)
     const JT mh = to_jt<JT>(-h);
     const JT *__restrict__ Dv = sm.D;
+#pragma unroll 1
     for (int p = sl; p < (f32 ? ns * ns : m.nJ); p += G) {
         const int2 meta = __ldg((f32 ? gl.j_meta32 : gl.j_meta) + p);
         const int len = meta.y >> 16;
@@ -672,6 +694,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             // species row: M_s sum nu_rs D_rk (the energy row follows from
             // the species rows below)
             auto coef = [](unsigned wv) -> JT { return (JT)small_int_to_float((int)wv >> 24); };
+#pragma unroll 1
             for (; q + 4 <= len; q += 4, e += 4 * G) {
                 const unsigned w0 = __ldg(gl.j_w + e), w1 = __ldg(gl.j_w + e + G), w2 = __ldg(gl.j_w + e + 2 * G),
                                w3 = __ldg(gl.j_w + e + 3 * G);
@@ -682,12 +705,14 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
                 a0 = fma(coef(w2), v2, a0);
                 a1 = fma(coef(w3), v3, a1);
             }
+#pragma unroll 1
             for (; q < len; ++q, e += G) {
                 const unsigned wv = __ldg(gl.j_w + e);
                 a0 = fma(coef(wv), Dv[wv & 0xffffffu], a0);
             }
             J = fma((JT)__ldg(m.spf + s * kSpStride), a0 + a1, J);
         } else {
+#pragma unroll 1
             for (; q + 4 <= len; q += 4, e += 4 * G) {
                 const int d0 = __ldg(gl.j_d + e), d1 = __ldg(gl.j_d + e + G), d2 = __ldg(gl.j_d + e + 2 * G),
                           d3 = __ldg(gl.j_d + e + 3 * G);
@@ -697,37 +722,44 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
                 a0 = fma((JT)__ldg(gl.j_c + e + 2 * G), v2, a0);
                 a1 = fma((JT)__ldg(gl.j_c + e + 3 * G), v3, a1);
             }
+#pragma unroll 1
             for (; q < len; ++q, e += G) a0 = fma((JT)__ldg(gl.j_c + e), Dv[__ldg(gl.j_d + e)], a0);
             J += a0 + a1;
         }
         sm.A[s * lda + k] = mh * J;
     }
     const JT dTdeJ = f32 ? (JT)dTdef : (JT)dTde;
+#pragma unroll 1
     for (int s = sl; s < (f32 ? ns : n); s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * dTdeJ);
     __syncwarp();
     if (f32) {
         // energy row -h J_ek = -sum_s e_f,s (-h J_sk): column sums over the
         // species rows, four partial sums in flight per lane
+#pragma unroll 1
         for (int k = sl; k < n; k += G) {
             JT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
             int s = 0;
+#pragma unroll 1
             for (; s + 4 <= ns; s += 4) {
                 a0 = fma((JT)__ldg(m.spf + s * kSpStride + 3), sm.A[s * lda + k], a0);
                 a1 = fma((JT)__ldg(m.spf + (s + 1) * kSpStride + 3), sm.A[(s + 1) * lda + k], a1);
                 a2 = fma((JT)__ldg(m.spf + (s + 2) * kSpStride + 3), sm.A[(s + 2) * lda + k], a2);
                 a3 = fma((JT)__ldg(m.spf + (s + 3) * kSpStride + 3), sm.A[(s + 3) * lda + k], a3);
             }
+#pragma unroll 1
             for (; s < ns; ++s) a0 = fma((JT)__ldg(m.spf + s * kSpStride + 3), sm.A[s * lda + k], a0);
             sm.A[ns * lda + k] = -((a0 + a1) + (a2 + a3));
         }
         __syncwarp();
     }
+#pragma unroll 1
     for (int i = sl; i < n; i += G) sm.A[i * lda + i] += (JT)1;
     if (f32) {
         // solve for (delta rho, delta e / S), S = E_scale / rho: the energy
         // row and column then sit on the species' scale, which keeps the
         // FP32 elimination well conditioned
         const JT S = to_jt<JT>(escale), iS = (JT)1 / S;
+#pragma unroll 1
         for (int k = sl; k < ns; k += G) {
             sm.A[ns * lda + k] *= iS;
             sm.A[k * lda + ns] *= S;
@@ -740,9 +772,11 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     //    (Sec. 3.2), ties to the lowest row; the pivot's reciprocal replaces
     //    the diagonal
     bool sing = false;
+#pragma unroll 1
     for (int j = 0; j < n; ++j) {
         unsigned long long best = 0;
         int bi = n;
+#pragma unroll 1
         for (int i = j + sl; i < n; i += G) {
             const unsigned long long kk = abs_key(sm.A[i * lda + j]);
             if (bi == n || kk > best) {
@@ -756,6 +790,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             Grp<G>::argmax(best, bi);
         if (best == 0 || key_is_inf(best, JT(0))) sing = true;
         if (bi != j && bi < n) {
+#pragma unroll 1
             for (int k = j + sl; k <= n; k += G) {
                 const JT t = sm.A[j * lda + k];
                 sm.A[j * lda + k] = sm.A[bi * lda + k];
@@ -768,6 +803,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         // cells at 1e-10)
         const JT inv = frcp(sm.A[j * lda + j]);
         if (!f32) {
+#pragma unroll 1
             for (int i = j + 1 + sl; i < n; i += G) sm.A[i * lda + j] *= inv;
             __syncwarp();
             if (sl == 0) sm.A[j * lda + j] = inv;
@@ -789,6 +825,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             const int q0 = (int)(((unsigned)sl * rc) >> 16), dq = (int)(((unsigned)G * rc) >> 16);
             int i = j + 1 + q0, k = j + 1 + (sl - q0 * cols);
             const int di = dq, dk = G - dq * cols;
+#pragma unroll 1
             for (; e < tot; e += G) {
                 sm.A[i * lda + k] -= sm.A[i * lda + j] * sm.A[j * lda + k];
                 i += di;
@@ -805,10 +842,12 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     }
     __syncwarp();
     // back substitution, U delta = y
+#pragma unroll 1
     for (int j = n - 1; j >= 0; --j) {
         const JT dj = sm.A[j * lda + n] * sm.A[j * lda + j];
         __syncwarp();
         if (sl == 0) sm.A[j * lda + n] = dj;
+#pragma unroll 1
         for (int i = sl; i < j; i += G) sm.A[i * lda + n] -= sm.A[i * lda + j] * dj;
         __syncwarp();
     }
@@ -822,6 +861,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     float nrmf = 0.f, desf = 0.f;
     int nonfinite = 0;
     const float escf = f32 ? d2f_rz(escale) : 0.f;
+#pragma unroll 1
     for (int i = sl; i < n; i += G) {
         float df = 0.f;
         double d;
@@ -915,6 +955,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, S
         while ((total >> level) > total - t_units) ++level;
         h = ldexp(b.dt, -level);
         ++attempts;
+#pragma unroll 1
         for (int i = sl; i < n; i += G) sm.x[i] = sm.x0[i];
         T = T0;
         k = 0;
@@ -930,8 +971,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, S
             start_substep();
     };
 
+#pragma unroll 1
     for (;;) {
         // refill free slots and settle every pending temperature recovery
+#pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             long long got = -1;
             if (state == kFree && sl == 0) got = (long long)atomicAdd(b.work_counter, 1ULL);
@@ -944,6 +987,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, S
                 cell = got;
                 iters = subs = fails = 0;
                 Tin = CUDART_NAN;
+#pragma unroll 1
                 for (int i = sl; i < n; i += G) {
                     const double v = i < ns ? b.rho[(size_t)i * b.ld + cell] : b.e[cell];
                     sm.x0[i] = v;
@@ -977,6 +1021,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, S
             bool ok = false;
             recover_T<G, sizeof(JT) == 4>(m, sm.x, sl, needT, T, Tr, ok);
             int neg = 0;
+#pragma unroll 1
             for (int i = sl; i < ns; i += G)
                 if (sm.x[i] < -atol_rho) neg = 1;
             neg = Grp<G>::any(neg);
@@ -1015,12 +1060,14 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, S
                 } else {
                     T = Tr;
                     // accept the substep
+#pragma unroll 1
                     for (int i = sl; i < n; i += G) sm.x0[i] = sm.x[i];
                     T0 = T;
                     t_units += total >> level;
                     ++subs;
                     if (level > 0) --level;
                     if (t_units == total) {
+#pragma unroll 1
                         for (int i = sl; i < n; i += G) {
                             if (i < ns)
                                 b.rho[(size_t)i * b.ld + cell] = sm.x[i];
