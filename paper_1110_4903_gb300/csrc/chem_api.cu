@@ -421,18 +421,63 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     for (size_t e = 0; e < t.sp_r.size(); ++e) t.sp_w.push_back(word(t.sp_r[e], t.sp_nui[e]));
     // the gather layouts for each lane count (chem_internal.h): list p on
     // lane p % G of pass p / G, its q-th term at base(pass) + q G + lane
+    // With `bank` (the shared-memory bank each term's operand sits in), the
+    // terms of each list are put in an order in which the lanes of a pass
+    // read distinct banks at each step where they can: the sum is the same
+    // up to the order of its FP32 additions.
     auto interleave = [](int nlists, const std::vector<int> &ptr, int G, std::vector<int2> &meta,
-                         std::vector<int> &pos, int tag_shift, const std::vector<int> *tags) {
+                         std::vector<int> &pos, int tag_shift, const std::vector<int> *tags,
+                         const std::vector<int> *bank = nullptr) {
         int base = 0;
         pos.assign(ptr.back(), -1);
         for (int P0 = 0; P0 < nlists; P0 += G) {
             const int P1 = std::min(nlists, P0 + G);
             int maxlen = 0;
             for (int q = P0; q < P1; ++q) maxlen = std::max(maxlen, ptr[q + 1] - ptr[q]);
+            // slot[e]: the step at which term e is read
+            std::vector<int> slot(ptr[P1] - ptr[P0], 0);
+            for (int q = P0; q < P1; ++q)
+                for (int i = 0; i < ptr[q + 1] - ptr[q]; ++i) slot[ptr[q] + i - ptr[P0]] = i;
+            if (bank) {
+                // greedy per step: the lists with the fewest terms left choose
+                // first, each the remaining term whose bank is least used
+                std::vector<std::vector<int>> left(P1 - P0);
+                for (int q = P0; q < P1; ++q)
+                    for (int e = ptr[q]; e < ptr[q + 1]; ++e) left[q - P0].push_back(e);
+                for (int i = 0; i < maxlen; ++i) {
+                    std::vector<int> act;
+                    for (int l = 0; l < P1 - P0; ++l)
+                        if (!left[l].empty()) act.push_back(l);
+                    std::stable_sort(act.begin(), act.end(),
+                                     [&](int a, int b) { return left[a].size() < left[b].size(); });
+                    int load[32] = {0};
+                    std::vector<int> seen;   // operands already read at this step (broadcast)
+                    for (int l : act) {
+                        int best = 0, best_cost = 1 << 30;
+                        for (int c = 0; c < (int)left[l].size(); ++c) {
+                            const int e = left[l][c], op = (*bank)[e];
+                            const bool dup = std::find(seen.begin(), seen.end(), op) != seen.end();
+                            const int cost = dup ? 0 : load[op & 31];
+                            if (cost < best_cost) {
+                                best_cost = cost;
+                                best = c;
+                            }
+                        }
+                        const int e = left[l][best];
+                        left[l].erase(left[l].begin() + best);
+                        slot[e - ptr[P0]] = i;
+                        const int op = (*bank)[e];
+                        if (std::find(seen.begin(), seen.end(), op) == seen.end()) {
+                            seen.push_back(op);
+                            ++load[op & 31];
+                        }
+                    }
+                }
+            }
             for (int q = P0; q < P1; ++q) {
                 const int len = ptr[q + 1] - ptr[q], lane = q - P0;
                 meta.push_back(make_int2(base + lane, (tags ? (*tags)[q] : 0) | (len << tag_shift)));
-                for (int i = 0; i < len; ++i) pos[ptr[q] + i] = base + i * G + lane;
+                for (int e = ptr[q]; e < ptr[q + 1]; ++e) pos[e] = base + slot[e - ptr[P0]] * G + lane;
             }
             base += maxlen * G;
         }
@@ -449,7 +494,7 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
             L.j_d[pos[e]] = t.j_d[e];
             L.j_c[pos[e]] = t.j_c[e];
         }
-        const int nw32 = interleave(ns * ns, t.j_ptr32, G, L.j_meta32, pos, 16, &t.j_sk32);
+        const int nw32 = interleave(ns * ns, t.j_ptr32, G, L.j_meta32, pos, 16, &t.j_sk32, &t.j_d32);
         L.j_w.assign(std::max(nw32, 1), 0u);
         for (size_t e = 0; e < pos.size(); ++e) L.j_w[pos[e]] = t.j_w[e];
         const int ni = interleave(t.n_items, t.it_ptr, G, L.it_meta, pos, 0, nullptr);
@@ -462,6 +507,19 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         if (L.it_meta.empty()) L.it_meta.push_back(make_int2(0, 0));
     }
     for (double v : t.sp) t.spf.push_back((float)v);
+    // the polynomial tables go coefficient-major (chem_internal.h): from
+    // [2 s + rg][c] to [2 c + rg][s]
+    auto coef_major = [ns](auto &v, int stride) {
+        auto o = v;
+        for (int s = 0; s < ns; ++s)
+            for (int rg = 0; rg < 2; ++rg)
+                for (int c = 0; c < stride; ++c)
+                    o[(size_t)(2 * c + rg) * ns + s] = v[((size_t)s * 2 + rg) * stride + c];
+        v.swap(o);
+    };
+    coef_major(t.thermo, kThermoStride);
+    coef_major(t.tpoly, kTpolyStride);
+    coef_major(t.tpoly_f, kTpolyFStride);
     // keep every array non-empty so device pointers are valid
     auto pad_f = [](std::vector<float> &v) { if (v.empty()) v.push_back(0.0f); };
     pad_f(t.rxn_df); pad_f(t.d_cef);
@@ -643,7 +701,7 @@ __global__ void state_from_tpy_kernel(DeviceMech m, long long n, long long ld, c
     for (int s = 0; s < m.ns; ++s) {
         const double rs = rt * Y[(size_t)s * ld + i];
         rho[(size_t)s * ld + i] = rs;
-        const double *th = m.thermo + (size_t)(s * 2 + (Ti > m.tmid[s] ? 1 : 0)) * kThermoStride;
+        const auto th = coef_row(m.thermo, m.ns, s, Ti > m.tmid[s] ? 1 : 0);
         const double hRT = th[0] + Ti * (th[5] + Ti * (th[6] + Ti * (th[7] + Ti * th[8]))) + th[9] * invT;
         ei += rs * (m.sp[s * kSpStride + 2] * Ti * (hRT - 1.0) - m.sp[s * kSpStride + 3]);
     }
@@ -662,7 +720,7 @@ __global__ void temperature_kernel(DeviceMech m, long long n, long long ld, cons
         const double invT = 1.0 / T;
         double f = 0.0, fp = 0.0;
         for (int s = 0; s < m.ns; ++s) {
-            const double *th = m.thermo + (size_t)(s * 2 + (T > m.tmid[s] ? 1 : 0)) * kThermoStride;
+            const auto th = coef_row(m.thermo, m.ns, s, T > m.tmid[s] ? 1 : 0);
             const double cpR = th[0] + T * (th[1] + T * (th[2] + T * (th[3] + T * th[4])));
             const double hRT = th[0] + T * (th[5] + T * (th[6] + T * (th[7] + T * th[8]))) + th[9] * invT;
             const double RM = m.sp[s * kSpStride + 2];

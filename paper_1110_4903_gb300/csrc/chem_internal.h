@@ -21,7 +21,13 @@ constexpr double kThi = 6000.0;
 constexpr int kTmaxIter = 50;          // temperature-recovery iterations
 constexpr double kTtol = 1e-13;        // |dT| <= kTtol * T ends the recovery
 
-// Thermo table row per species and range (16 doubles):
+// Polynomial tables are stored coefficient-major, so that the lanes of a
+// warp, which hold consecutive species, read consecutive words: coefficient
+// c of species s in temperature range rg (0: T <= T_mid, 1: above) at
+// [(2 c + rg) ns + s].  (The reaction tables stay row-major: a lane reads
+// a reaction's row with two 16-byte loads, which measured faster.)
+//
+// Thermo table, per species and range (16 coefficients):
 //   0..4  cp/R coefficients a1..a5
 //   5..8  h/RT coefficients a2/2, a3/3, a4/4, a5/5 (a1 and a6 shared)
 //   9     a6
@@ -29,12 +35,12 @@ constexpr double kTtol = 1e-13;        // |dT| <= kTtol * T ends the recovery
 //   13    a7
 constexpr int kThermoStride = 16;
 
-// Energy polynomials per species and range (12 doubles), the NASA-7 forms
+// Energy polynomials per species and range (12 coefficients), the NASA-7 forms
 // multiplied out with R/M and shifted by the formation energy:
 //   0..5  e_s(T) - e_f,s = c0 + c1 T + ... + c5 T^5  (c0 = R/M a6 - e_f,
 //         c1 = R/M (a1 - 1), c_i = R/M a_i / i for i = 2..5)
 //   6..10 c_v,s(T) = R/M (cp/R - 1) = d0 + d1 T + ... + d4 T^4
-// and an FP32 copy of d0..d4 (8 floats per row).
+// and an FP32 copy of d0..d4 (8 coefficients).
 constexpr int kTpolyStride = 12;
 constexpr int kTpolyFStride = 8;
 
@@ -106,10 +112,10 @@ struct DeviceMech {
     int nJ;                     // Jacobian entries gathered by the FP64 kernel: ns*ns species,
                                 // ns energy row (the FP32 kernel gathers the ns*ns species)
     int n_items;                // species-gather work items
-    const double *thermo;       // [ns][2][16]
+    const double *thermo;       // [16][2][ns] (coefficient-major, above)
     const double *tmid;         // [ns] (positive: compared as integers)
-    const double *tpoly;        // [ns][2][12] energy and heat-capacity polynomials
-    const float *tpoly_f;       // [ns][2][8] heat-capacity polynomial in FP32
+    const double *tpoly;        // [12][2][ns] energy and heat-capacity polynomials
+    const float *tpoly_f;       // [8][2][ns] heat-capacity polynomial in FP32
     const double *sp;           // [ns][4]
     const double *rxn_d;        // [nr][4]
     const int *rxn_f;           // [nr][2]
@@ -172,6 +178,21 @@ constexpr int kBlockHeaderBytes = 0;
 //             JT), dead once the D entries exist, and the augmented matrix
 //             n x (n+1) in JT, which is written after that
 __host__ __device__ inline long long align16(long long b) { return (b + 15) / 16 * 16; }
+
+#ifdef __CUDACC__
+// The coefficients of one species and range of a coefficient-major
+// polynomial table, read through the read-only path: p[c].
+template <typename T>
+struct CoefRow {
+    const T *p;
+    int stride;
+    __device__ __forceinline__ T operator[](int c) const { return __ldg(p + (size_t)c * stride); }
+};
+template <typename T>
+__device__ __forceinline__ CoefRow<T> coef_row(const T *tab, int ns, int s, int rg) {
+    return CoefRow<T>{tab + (size_t)rg * ns + s, 2 * ns};
+}
+#endif
 __host__ __device__ inline long long slot_dbl_bytes(int ns, int jt) {
     const int n = ns + 1;
     return align16((2LL * n + 2LL * (ns + 1) + (jt == 8 ? (long long)(ns + 1) + ns : 0)) * 8);

@@ -232,13 +232,14 @@ __device__ __forceinline__ double fexp(double x, const double *tab) {
     return __longlong_as_double(__double_as_longlong(y) + (k << 52));
 }
 
-// NASA-7 entropy from a 16-double thermo row (layout in chem_internal.h)
-__device__ __forceinline__ double nasa_s(const double *th, double T, double lnT) {
+// NASA-7 entropy from the thermo coefficients of one species and range
+// (layout in chem_internal.h)
+__device__ __forceinline__ double nasa_s(const CoefRow<double> &th, double T, double lnT) {
     return th[0] * lnT + T * (th[1] + T * (th[10] + T * (th[11] + T * th[12]))) + th[13];
 }
-// range of species s at T (T > T_mid: high range), as a row index
-__device__ __forceinline__ int thermo_range_row(const DeviceMech &m, int s, long long Tbits) {
-    return s * 2 + (Tbits > __ldg(reinterpret_cast<const long long *>(m.tmid) + s) ? 1 : 0);
+// range of species s at T (1: T > T_mid, the high range)
+__device__ __forceinline__ int thermo_range(const DeviceMech &m, int s, long long Tbits) {
+    return Tbits > __ldg(reinterpret_cast<const long long *>(m.tmid) + s) ? 1 : 0;
 }
 
 // Temperature recovery from (rho_s, e) for every slot whose `need` is set:
@@ -266,19 +267,16 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
         float fpf = 0.f;
 #pragma unroll 1
         for (int s = sl; s < ns; s += G) {
-            const int row = thermo_range_row(m, s, Tb);
-            const double *c = m.tpoly + (size_t)row * kTpolyStride;
-            const double es = fma(fma(fma(fma(fma(__ldg(c + 5), T, __ldg(c + 4)), T, __ldg(c + 3)), T, __ldg(c + 2)), T,
-                                      __ldg(c + 1)), T, __ldg(c));
+            const int rg = thermo_range(m, s, Tb);
+            const auto c = coef_row(m.tpoly, ns, s, rg);
+            const double es = fma(fma(fma(fma(fma(c[5], T, c[4]), T, c[3]), T, c[2]), T, c[1]), T, c[0]);
             f = fma(x[s], es, f);
             if (F32) {
-                const float *d = m.tpoly_f + (size_t)row * kTpolyFStride;
-                const float cv = fmaf(fmaf(fmaf(fmaf(__ldg(d + 4), Tf, __ldg(d + 3)), Tf, __ldg(d + 2)), Tf, __ldg(d + 1)),
-                                      Tf, __ldg(d));
+                const auto d = coef_row(m.tpoly_f, ns, s, rg);
+                const float cv = fmaf(fmaf(fmaf(fmaf(d[4], Tf, d[3]), Tf, d[2]), Tf, d[1]), Tf, d[0]);
                 fpf = fmaf(d2f_rz(x[s]), cv, fpf);
             } else {
-                const double cv = fma(fma(fma(fma(__ldg(c + 10), T, __ldg(c + 9)), T, __ldg(c + 8)), T, __ldg(c + 7)), T,
-                                      __ldg(c + 6));
+                const double cv = fma(fma(fma(fma(c[10], T, c[9]), T, c[8]), T, c[7]), T, c[6]);
                 fp = fma(x[s], cv, fp);
             }
         }
@@ -440,8 +438,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const double ci = xs * __ldg(spr + 1);
         sm.c[s] = ci;
         ctot += ci;
-        const int row = thermo_range_row(m, s, Tb);
-        const double *th = m.thermo + (size_t)row * kThermoStride;
+        const int rg = thermo_range(m, s, Tb);
+        const auto th = coef_row(m.thermo, ns, s, rg);
         const double hRT = th[0] + T * (th[5] + T * (th[6] + T * (th[7] + T * th[8]))) + th[9] * invT;
         const double sR = nasa_s(th, T, lnT);
         const double RM = __ldg(spr + 2);
@@ -449,16 +447,14 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const double es = RM * T * (hRT - 1.0) - __ldg(spr + 3);
         if (f32) {
             sm.esJ[s] = to_jt<JT>(es);
-            const float *d = m.tpoly_f + (size_t)row * kTpolyFStride;
-            const float cv = fmaf(fmaf(fmaf(fmaf(__ldg(d + 4), Tf, __ldg(d + 3)), Tf, __ldg(d + 2)), Tf, __ldg(d + 1)),
-                                  Tf, __ldg(d));
+            const auto d = coef_row(m.tpoly_f, ns, s, rg);
+            const float cv = fmaf(fmaf(fmaf(fmaf(d[4], Tf, d[3]), Tf, d[2]), Tf, d[1]), Tf, d[0]);
             rhocvf = fmaf(d2f_rz(xs), cv, rhocvf);
             sm.cJ[s] = to_jt<JT>(ci);
             sm.hJ[s] = to_jt<JT>(hRT);
         } else {
-            const double *c = m.tpoly + (size_t)row * kTpolyStride;
-            const double cv = fma(fma(fma(fma(__ldg(c + 10), T, __ldg(c + 9)), T, __ldg(c + 8)), T, __ldg(c + 7)), T,
-                                  __ldg(c + 6));
+            const auto c = coef_row(m.tpoly, ns, s, rg);
+            const double cv = fma(fma(fma(fma(c[10], T, c[9]), T, c[8]), T, c[7]), T, c[6]);
             rhocv = fma(xs, cv, rhocv);
             sm.hRT[s] = hRT;
             sm.es[s] = es;
@@ -487,11 +483,25 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     // 2. rates per reaction: Eq. 23 forward rate, Eq. 24 equilibrium
     //    constant, Eq. 25 progress rate, and their temperature derivatives
     const JT iT = to_jt<JT>(invT);
+    // (the next reaction's parameters are loaded while this one is
+    // evaluated: the loop is kept rolled, so nothing else would overlap them)
+    static_assert(kRxnDStride == 4, "a reaction's FP64 parameters are two double2");
+    double2 nAb = make_double2(0.0, 0.0), nEd = make_double2(0.0, 0.0);
+    int2 nf = make_int2(0, 0);
+    auto load_rxn = [&](int r) {
+        if (r < nr) {
+            const double2 *rd = reinterpret_cast<const double2 *>(m.rxn_d + (size_t)r * kRxnDStride);
+            nAb = __ldg(rd);
+            nEd = __ldg(rd + 1);
+            nf = __ldg(reinterpret_cast<const int2 *>(m.rxn_f) + r);
+        }
+    };
+    load_rxn(sl);
 #pragma unroll 1
     for (int r = sl; r < nr; r += G) {
-        const double *rd = m.rxn_d + (size_t)r * kRxnDStride;
-        const double lnA = __ldg(rd + 0), beta = __ldg(rd + 1), EaR = __ldg(rd + 2), dnu = __ldg(rd + 3);
-        const int fr = __ldg(m.rxn_f + 2 * r), fpw = __ldg(m.rxn_f + 2 * r + 1);
+        const double lnA = nAb.x, beta = nAb.y, EaR = nEd.x, dnu = nEd.y;
+        const int fr = nf.x, fpw = nf.y;
+        load_rxn(r + G);
         const int a0 = fr & 0xff, a1 = (fr >> 8) & 0xff, a2 = (fr >> 16) & 0xff;
         const int b0 = fpw & 0xff, b1 = (fpw >> 8) & 0xff, b2 = (fpw >> 16) & 0xff;
         const double Pf = sm.c[a0] * sm.c[a1] * sm.c[a2];
@@ -513,7 +523,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         sm.Q[r] = CM * q;   // in the D region until phase 4
         if (f32) {
             // Jacobian-only quantities in FP32 from FP32 copies
-            const float* rf = m.rxn_df + (size_t)r * kRxnDStride;
+            const float *rf = m.rxn_df + (size_t)r * kRxnDStride;
             // (products formed in FP32 from converted factors: the FP64
             // pipe keeps to the rates the residual needs)
             const JT CMf = to_jt<JT>(CM);
