@@ -165,18 +165,18 @@ enum CellStatus { kCellOk = 0, kCellNewtonFailed = 1, kCellTFailed = 2, kCellBad
 constexpr int kBlockHeaderBytes = 0;
 
 // Bytes of one cell slot, in this order (jt = sizeof of the Jacobian type):
-//   doubles   x, x0 (n each); c, gRT with a sentinel (ns+1 each); FP64 path
-//             also hRT (ns+1, with the sentinel) and es (ns)
+//   doubles   x, x0 (n each); FP64 path also es (ns)
 //   JT        FP64 path: dTdr (ns), w, u (ns+1 each: the species rows' T
 //             derivative and third-body vectors, then the energy row's), rhs (n)
-//             FP32 path: w, u (ns each), cJ, hJ (ns+1 each: c and h/RT with the
-//             sentinel), es (ns), rhs (n)
+//             FP32 path: w, u, es (ns each), rhs (n)
 //   D region  first Q (nr doubles) and the species-gather partial sums (per
 //             item: sum nu Q in FP64, then sum nu dQ/dT and sum nu q_tb in JT),
 //             which are dead once the D entries (nD in JT) are written
-//   union     the per-reaction values dQdT, A1, A2 (nr JT each) and qtb (ntb
-//             JT), dead once the D entries exist, and the augmented matrix
-//             n x (n+1) in JT, which is written after that
+//   union     while the rates, sources and D entries are formed: the species
+//             values with a sentinel (ns+1 each) c, em, emi (doubles), FP64
+//             path hRT (double), ek (int), FP32 path cJ, hJ (float), then the
+//             per-reaction values dQdT, A1, A2 (nr JT each) and qtb (ntb JT);
+//             after the D entries: the augmented matrix n x (n+1) in JT
 __host__ __device__ inline long long align16(long long b) { return (b + 15) / 16 * 16; }
 
 #ifdef __CUDACC__
@@ -195,12 +195,19 @@ __device__ __forceinline__ CoefRow<T> coef_row(const T *tab, int ns, int s, int 
 #endif
 __host__ __device__ inline long long slot_dbl_bytes(int ns, int jt) {
     const int n = ns + 1;
-    return align16((2LL * n + 2LL * (ns + 1) + (jt == 8 ? (long long)(ns + 1) + ns : 0)) * 8);
+    return align16((2LL * n + (jt == 8 ? ns : 0)) * 8);
 }
 __host__ __device__ inline long long slot_small_bytes(int ns, int jt) {
     const int n = ns + 1;
-    const long long cnt = jt == 8 ? (long long)ns + 2LL * (ns + 1) + n : 2LL * ns + 2LL * (ns + 1) + ns + n;
+    const long long cnt = jt == 8 ? (long long)ns + 2LL * (ns + 1) + n : 3LL * ns + n;
     return align16(cnt * jt);
+}
+// species part of the union: c, em, emi (+ hRT) doubles, ek ints (+ cJ, hJ
+// floats), padded to 16 bytes so the per-reaction arrays that follow are
+// aligned
+__host__ __device__ inline long long slot_union_species_bytes(int ns, int jt) {
+    const long long m = ns + 1;
+    return align16(m * 8 * (jt == 8 ? 4 : 3) + m * 4 * (jt == 8 ? 1 : 3));
 }
 __host__ __device__ constexpr long long item_bytes(int jt) { return 8 + 2LL * jt; }
 __host__ __device__ inline long long slot_dreg_bytes(int nr, int nD, int n_items, int jt) {
@@ -209,7 +216,8 @@ __host__ __device__ inline long long slot_dreg_bytes(int nr, int nD, int n_items
 }
 __host__ __device__ inline long long slot_union_bytes(int ns, int nr, int ntb, int jt) {
     const int n = ns + 1;
-    const long long a = 3LL * nr * jt + (long long)ntb * jt, b = (long long)n * (n + 1) * jt;
+    const long long a = slot_union_species_bytes(ns, jt) + 3LL * nr * jt + (long long)ntb * jt,
+                    b = (long long)n * (n + 1) * jt;
     return align16(a > b ? a : b);
 }
 __host__ __device__ inline long long slot_bytes_for(const DeviceMech &m, int jt) {

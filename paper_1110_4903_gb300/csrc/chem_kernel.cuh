@@ -232,6 +232,57 @@ __device__ __forceinline__ double fexp(double x, const double *tab) {
     return __longlong_as_double(__double_as_longlong(y) + (k << 52));
 }
 
+// exp(x) = y 2^k with y in [0.99, 2.01]: the reduction of fexp without its
+// final scaling, so that products of many exponentials can be formed
+// without overflow.  512 <= |x| < 1024 takes the square of exp(x/2);
+// beyond that (and for infinities) k saturates at +-4096 with y = 1, and
+// a NaN x gives a NaN y.
+__device__ __forceinline__ void split_exp(double x, const double *tab, double &y, int &k) {
+    const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
+    const unsigned ex = (hi >> 20) & 0x7ffu;
+    bool sq = false;
+    if (ex > 0x407u) {
+        if (ex > 0x408u) {
+            const bool nan = ex == 0x7ffu && ((hi & 0xfffffu) | (unsigned)__double_as_longlong(x));
+            y = nan ? x : 1.0;
+            k = (hi >> 31) ? -4096 : 4096;
+            return;
+        }
+        x *= 0.5;
+        sq = true;
+    }
+    const double kShift = 6755399441055744.0;               // 1.5 * 2^52
+    const double t = fma(x, 369.3299304675746, kShift);     // x * 256/ln2, rounded
+    const int n = (int)(unsigned)__double_as_longlong(t);
+    const double nd = t - kShift;
+    double r = fma(nd, -0x1.62e42fefa0000p-9, x);
+    r = fma(nd, -0x1.cf79abc9e3b3ap-48, r);
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
+    p = fma(r, p, 0.5);
+    p = fma(r, p, 1.0);
+    p *= r;
+    const double s = __ldg(tab + (n & (kExpTab - 1)));
+    y = fma(s, p, s);
+    k = n >> 8;
+    if (sq) {
+        y *= y;
+        k *= 2;
+    }
+}
+// v 2^k on the exponent bits for a normal v; zero, subnormal, infinite and
+// NaN v come back unchanged, a result below the normal range is a signed
+// zero and one above it an infinity.
+__device__ __forceinline__ double scale_pow2(double v, int k) {
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0 || e == 0x7ff) return v;
+    const int ne = e + k;
+    const long long sgn = b & (long long)0x8000000000000000ULL;
+    if (ne <= 0) return __longlong_as_double(sgn);
+    if (ne >= 0x7ff) return __longlong_as_double(sgn | 0x7ff0000000000000LL);
+    return __longlong_as_double(b + ((long long)k << 52));
+}
+
 // NASA-7 entropy from the thermo coefficients of one species and range
 // (layout in chem_internal.h)
 __device__ __forceinline__ double nasa_s(const CoefRow<double> &th, double T, double lnT) {
@@ -357,26 +408,22 @@ __device__ __forceinline__ void lu_update_by_columns(JT *A, int lda, int n, int 
 
 template <typename JT>
 struct SlotMem {
-    double *x, *x0, *c, *hRT, *gRT, *es, *Q, *part;
+    double *x, *x0, *c, *hRT, *es, *em, *emi, *Q, *part;
+    int *ek;
     JT *D, *dTdr, *w, *u, *A, *dQdT, *qtb, *A1, *A2, *rhs;
     JT *cJ, *hJ, *esJ;   // FP32 path: c, h/RT and e^sens in the Jacobian type
     // layout and sizes in chem_internal.h (slot_bytes_for); the FP64 path has
-    // no FP32 copies (cJ = c, hJ = hRT) and the FP32 path no FP64 hRT, es
-    // or dTdr
+    // no FP32 copies (cJ = c, hJ = hRT), the FP32 path no FP64 hRT, es or
+    // dTdr.  The species values of the rates (c, the split exponentials em,
+    // emi, ek, and h/RT) share the union with the matrix: they are written
+    // again every iteration, sentinel included.
     __device__ __forceinline__ void carve(char *base, const DeviceMech &m) {
         const int ns = m.ns, n = ns + 1, nr = m.nr;
         constexpr int jt = (int)sizeof(JT);
         double *p = reinterpret_cast<double *>(base);
         x = p;
         x0 = x + n;
-        c = x0 + n;
-        gRT = c + ns + 1;
-        if (jt == 8) {
-            hRT = gRT + ns + 1;
-            es = hRT + ns + 1;
-        } else {
-            hRT = es = nullptr;
-        }
+        es = jt == 8 ? x0 + n : nullptr;
         char *q = base + slot_dbl_bytes(ns, jt);
         JT *t = reinterpret_cast<JT *>(q);
         if (jt == 8) {
@@ -384,16 +431,12 @@ struct SlotMem {
             w = dTdr + ns;
             u = w + ns + 1;
             rhs = u + ns + 1;
-            cJ = reinterpret_cast<JT *>(c);
-            hJ = reinterpret_cast<JT *>(hRT);
             esJ = reinterpret_cast<JT *>(es);
         } else {
             dTdr = nullptr;
             w = t;
             u = w + ns;
-            cJ = u + ns;
-            hJ = cJ + ns + 1;
-            esJ = hJ + ns + 1;
+            esJ = u + ns;
             rhs = esJ + ns;
         }
         q += slot_small_bytes(ns, jt);
@@ -402,12 +445,25 @@ struct SlotMem {
         part = Q + nr;
         D = reinterpret_cast<JT *>(q);
         q += slot_dreg_bytes(nr, m.nD, m.n_items, jt);
-        // union: per-reaction values, then (after the D entries) the matrix
-        dQdT = reinterpret_cast<JT *>(q);
+        // union: species values and per-reaction values, then (after the D
+        // entries) the matrix
+        A = reinterpret_cast<JT *>(q);
+        c = reinterpret_cast<double *>(q);
+        em = c + ns + 1;
+        emi = em + ns + 1;
+        hRT = jt == 8 ? emi + ns + 1 : nullptr;
+        ek = reinterpret_cast<int *>(emi + (jt == 8 ? 2 : 1) * (ns + 1));
+        if (jt == 8) {
+            cJ = reinterpret_cast<JT *>(c);
+            hJ = reinterpret_cast<JT *>(hRT);
+        } else {
+            cJ = reinterpret_cast<JT *>(ek + ns + 1);
+            hJ = cJ + ns + 1;
+        }
+        dQdT = reinterpret_cast<JT *>(q + slot_union_species_bytes(ns, jt));
         A1 = dQdT + nr;
         A2 = A1 + nr;
         qtb = A2 + nr;
-        A = reinterpret_cast<JT *>(q);
     }
 };
 
@@ -443,7 +499,14 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const double hRT = th[0] + T * (th[5] + T * (th[6] + T * (th[7] + T * th[8]))) + th[9] * invT;
         const double sR = nasa_s(th, T, lnT);
         const double RM = __ldg(spr + 2);
-        sm.gRT[s] = hRT - sR;
+        // exp(g_s/RT - ln(P_a/RT)) split into mantissa and power of two,
+        // for the equilibrium constants (phase 2)
+        double ey;
+        int eK;
+        split_exp(hRT - sR - lnPaRT, tab, ey, eK);
+        sm.em[s] = ey;
+        sm.emi[s] = frcp(ey);
+        sm.ek[s] = eK;
         const double es = RM * T * (hRT - 1.0) - __ldg(spr + 3);
         if (f32) {
             sm.esJ[s] = to_jt<JT>(es);
@@ -460,9 +523,18 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             sm.es[s] = es;
         }
     }
-    if (f32 && sl == 0) {
-        sm.cJ[ns] = (JT)1;
-        sm.hJ[ns] = (JT)0;
+    if (sl == 0) {
+        // sentinel species: concentration 1, no Gibbs or enthalpy contribution
+        sm.c[ns] = 1.0;
+        sm.em[ns] = 1.0;
+        sm.emi[ns] = 1.0;
+        sm.ek[ns] = 0;
+        if (f32) {
+            sm.cJ[ns] = (JT)1;
+            sm.hJ[ns] = (JT)0;
+        } else {
+            sm.hRT[ns] = 0.0;
+        }
     }
     ctot = Grp<G>::sum(ctot);
     double dTde;
@@ -506,11 +578,16 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const int b0 = fpw & 0xff, b1 = (fpw >> 8) & 0xff, b2 = (fpw >> 16) & 0xff;
         const double Pf = sm.c[a0] * sm.c[a1] * sm.c[a2];
         const double Pb = sm.c[b0] * sm.c[b1] * sm.c[b2];
-        const double sg = (sm.gRT[b0] + sm.gRT[b1] + sm.gRT[b2]) - (sm.gRT[a0] + sm.gRT[a1] + sm.gRT[a2]);
         const double lnkf = lnA + beta * lnT - EaR * invT;
-        const double lnKc = dnu * lnPaRT - sg;
         const double kf = fexp(lnkf, tab);
-        const double kb = fexp(lnkf - lnKc, tab);
+        // K_b = K_f / K_c with 1/K_c = (RT/P_a)^dnu exp(dG/RT) (Eq. 24) as
+        // the product over the factor slots of the species' exp(g/RT) (RT/P_a)
+        // (products) and their inverses (reactants), the sentinel giving 1:
+        // mantissas multiplied in FP64, powers of two added as integers, so no
+        // exponential per reaction and no overflow in the partial products
+        const int K2 = (sm.ek[b0] + sm.ek[b1] + sm.ek[b2]) - (sm.ek[a0] + sm.ek[a1] + sm.ek[a2]);
+        const double Pm = ((sm.em[b0] * sm.em[b1]) * sm.em[b2]) * ((sm.emi[a0] * sm.emi[a1]) * sm.emi[a2]);
+        const double kb = scale_pow2(kf * Pm, K2);
         double CM = 1.0;
         const bool tb = (fr >> 24) & 1;
         if (tb) {
@@ -931,12 +1008,6 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, S
     const long long sbytes = slot_bytes_for(m, (int)sizeof(JT));
     SlotMem<JT> sm;
     sm.carve(smem + (size_t)(warp * S + slot) * sbytes, m);
-    // sentinel species: concentration 1, no Gibbs or enthalpy contribution
-    if (sl == 0) {
-        sm.c[ns] = 1.0;
-        if (sizeof(JT) == 8) sm.hRT[ns] = 0.0;
-        sm.gRT[ns] = 0.0;
-    }
     __syncthreads();
 
     int state = kFree;
