@@ -60,8 +60,9 @@ constexpr int kRxnFStride = 2;
 // Species-gather chunk length (entries per work item).
 constexpr int kChunk = 8;
 
-// Threads per block of the step kernel at most (its launch bounds).
-constexpr int kMaxBlockThreads = 192;
+// Threads per block of the step kernel at most (its launch bounds: two
+// such blocks per SM, at most 102 registers per thread).
+constexpr int kMaxBlockThreads = 320;
 
 // Entries of the exp table (2^(j/kExpTab)).
 constexpr int kExpTab = 256;
@@ -176,7 +177,9 @@ constexpr int kBlockHeaderBytes = 0;
 //             values with a sentinel (ns+1 each) c, em, emi (doubles), FP64
 //             path hRT (double), ek (int), FP32 path cJ, hJ (float), then the
 //             per-reaction values dQdT, A1, A2 (nr JT each) and qtb (ntb JT);
-//             after the D entries: the augmented matrix n x (n+1) in JT
+//             after the D entries: the augmented matrix in JT, n x (n+1) on
+//             the FP64 path, ns x (ns+1) on the FP32 path (energy unknown
+//             eliminated)
 __host__ __device__ inline long long align16(long long b) { return (b + 15) / 16 * 16; }
 
 #ifdef __CUDACC__
@@ -216,8 +219,9 @@ __host__ __device__ inline long long slot_dreg_bytes(int nr, int nD, int n_items
 }
 __host__ __device__ inline long long slot_union_bytes(int ns, int nr, int ntb, int jt) {
     const int n = ns + 1;
+    const int N = jt == 8 ? n : ns;
     const long long a = slot_union_species_bytes(ns, jt) + 3LL * nr * jt + (long long)ntb * jt,
-                    b = (long long)n * (n + 1) * jt;
+                    b = (long long)N * (N + 1) * jt;
     return align16(a > b ? a : b);
 }
 __host__ __device__ inline long long slot_bytes_for(const DeviceMech &m, int jt) {

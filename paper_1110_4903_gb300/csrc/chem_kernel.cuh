@@ -21,10 +21,10 @@
 //     evaluation, and the temperature recovery a multiplied-out polynomial.
 // The mixed path (JT = float) keeps the FP64 residual, rates, sources and
 // temperature, and moves everything that only feeds the Jacobian to FP32;
-// its LU is organised by columns, and its energy row is formed from the
-// species rows.  It is bound by latency, so its slot layout is cut to what
-// it reads (18 warps per SM at 36 species).
-//   Code size: with 18 warps at different phases, the instructions of one
+// it eliminates the energy unknown through the conservation of total
+// energy, and its LU is organised by columns.  It is bound by latency, so
+// its slot layout is cut to what it reads (20 warps per SM at 36 species).
+//   Code size: with 20 warps at different phases, the instructions of one
 // Newton iteration have to stay in the SM's instruction caches.  The
 // compiler's unrolling of the many short runtime-count loops made the mixed
 // kernel 114 KB, and instruction fetch its first stall; every loop below is
@@ -473,9 +473,12 @@ struct SlotMem {
 template <int G, typename JT>
 __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem<JT> &sm, int sl,
                                  double T, double h, double atol_rho, double atol_e, double rtol,
-                                 double escale, double &norm, bool &bad, double &T_pred) {
+                                 double &norm, bool &bad, double &T_pred) {
     const int ns = m.ns, nr = m.nr, n = ns + 1, lda = n + 1;
     constexpr bool f32 = sizeof(JT) == 4;
+    // the linear system solved: FP64 the full (n) x (n) one; FP32 the
+    // species block with the energy unknown eliminated (phase 5)
+    const int N = f32 ? ns : n, ldA = N + 1;
     const double invT = frcp(T);
     const double lnT = log(T);
     const double lnPaRT = log(kPa / kR) - lnT;
@@ -658,7 +661,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         pj[1] = squ;
     }
     __syncwarp();
-    double wde = 0.0;
+    double wde = 0.0, dEt = 0.0;
     JT We = 0, Ue = 0;
 #pragma unroll 1
     for (int s = sl; s < ns; s += G) {
@@ -679,16 +682,29 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const JT efJ = f32 ? (JT)__ldg(m.spf + s * kSpStride + 3) : (JT)ef;
         const double wds = M * sq;
         // right-hand side -F_s = -(x_s - x0_s - h wdot_s), FP64 until stored
-        sm.rhs[s] = to_jt<JT>(-(sm.x[s] - sm.x0[s] - h * wds));
+        const double dx = sm.x[s] - sm.x0[s];
+        sm.rhs[s] = to_jt<JT>(-(dx - h * wds));
         const JT ws = MJ * sdq, us = MJ * squ;
         sm.w[s] = ws;
         sm.u[s] = us;
-        wde -= ef * wds;
-        We += efJ * ws;
-        Ue += efJ * us;
+        if (f32) {
+            dEt = fma(ef, dx, dEt);
+        } else {
+            wde -= ef * wds;
+            We += efJ * ws;
+            Ue += efJ * us;
+        }
     }
-    wde = Grp<G>::sum(wde);
-    if (sl == 0) sm.rhs[ns] = to_jt<JT>(-(sm.x[ns] - sm.x0[ns] - h * wde));
+    // FP32 path: the total-energy residual R_E = F_e + sum_s e_f,s F_s =
+    // (x_e - x0_e) + sum_s e_f,s (x_s - x0_s), in which the sources cancel
+    // (Omega_e = -sum_s e_f,s wdot_s); it replaces the energy equation
+    double RE = 0.0;
+    if (f32) {
+        RE = Grp<G>::sum(dEt) + (sm.x[ns] - sm.x0[ns]);
+    } else {
+        wde = Grp<G>::sum(wde);
+        if (sl == 0) sm.rhs[ns] = to_jt<JT>(-(sm.x[ns] - sm.x0[ns] - h * wde));
+    }
     if (!f32) {
         // the energy row's rank-one parts: J_ek = -sum_s e_f,s J_sk
         We = Grp<G>::sum(We);
@@ -757,15 +773,29 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     __syncwarp();
     // the per-reaction arrays are dead from here on; the matrix takes their place
 
-    // 5. right-hand side -F = -(x - x0 - h Omega(x)) into the matrix
+    // 5. right-hand side into the matrix.  FP64: -F = -(x - x0 - h Omega(x)).
+    //    FP32: the energy unknown is eliminated.  The energy row of I - hJ
+    //    is [e_f, 1] - sum_s e_f,s (row s) (J_ek = -sum_s e_f,s J_sk), so
+    //    with the species equations it reduces to the conservation law
+    //    de = -R_E - e_f . drho; substituted into the species rows, whose
+    //    energy-column entry is a_s = -h w_s dT/de, it leaves
+    //      sum_k (A_sk - a_s e_f,k) drho_k = -F_s + a_s R_E,
+    //    the same solution as the full system in exact arithmetic, with one
+    //    unknown fewer and no energy row to form or scale
+    const JT mh = to_jt<JT>(-h);
+    if (f32) {
+        const JT cRE = mh * (JT)dTdef * d2f_rz(RE);
 #pragma unroll 1
-    for (int i = sl; i < n; i += G) sm.A[i * lda + n] = sm.rhs[i];
+        for (int i = sl; i < N; i += G) sm.A[i * ldA + N] = fma(sm.w[i], cRE, sm.rhs[i]);
+    } else {
+#pragma unroll 1
+        for (int i = sl; i < n; i += G) sm.A[i * lda + n] = sm.rhs[i];
+    }
 
     // 6. species and energy rows of -h J, density columns (longest gather
     //    lists first, so the lanes of a pass run lists of nearly equal
     //    length), then the temperature column
     //    (four terms in flight per trip, two accumulators)
-    const JT mh = to_jt<JT>(-h);
     const JT *__restrict__ Dv = sm.D;
 #pragma unroll 1
     for (int p = sl; p < (f32 ? ns * ns : m.nJ); p += G) {
@@ -773,7 +803,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const int len = meta.y >> 16;
         const int s = (meta.y >> 8) & 0xff, k = meta.y & 0xff;
         const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
-        const JT dTdrk = f32 ? -sm.esJ[k] * (JT)dTdef : sm.dTdr[k];
+        // (FP32: the reduced system's column k: dT/drho_k - e_f,k dT/de)
+        const JT dTdrk = f32 ? -(sm.esJ[k] + (JT)__ldg(m.spf + k * kSpStride + 3)) * (JT)dTdef : sm.dTdr[k];
         JT J = sm.w[s] * dTdrk + sm.u[s] * invMk;
         JT a0 = 0, a1 = 0;
         int e = meta.x, q = 0;
@@ -813,46 +844,15 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             for (; q < len; ++q, e += G) a0 = fma((JT)__ldg(gl.j_c + e), Dv[__ldg(gl.j_d + e)], a0);
             J += a0 + a1;
         }
-        sm.A[s * lda + k] = mh * J;
+        sm.A[s * ldA + k] = mh * J;
     }
-    const JT dTdeJ = f32 ? (JT)dTdef : (JT)dTde;
+    if (!f32) {
 #pragma unroll 1
-    for (int s = sl; s < (f32 ? ns : n); s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * dTdeJ);
+        for (int s = sl; s < n; s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * (JT)dTde);
+    }
     __syncwarp();
-    if (f32) {
-        // energy row -h J_ek = -sum_s e_f,s (-h J_sk): column sums over the
-        // species rows, four partial sums in flight per lane
 #pragma unroll 1
-        for (int k = sl; k < n; k += G) {
-            JT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-            int s = 0;
-#pragma unroll 1
-            for (; s + 4 <= ns; s += 4) {
-                a0 = fma((JT)__ldg(m.spf + s * kSpStride + 3), sm.A[s * lda + k], a0);
-                a1 = fma((JT)__ldg(m.spf + (s + 1) * kSpStride + 3), sm.A[(s + 1) * lda + k], a1);
-                a2 = fma((JT)__ldg(m.spf + (s + 2) * kSpStride + 3), sm.A[(s + 2) * lda + k], a2);
-                a3 = fma((JT)__ldg(m.spf + (s + 3) * kSpStride + 3), sm.A[(s + 3) * lda + k], a3);
-            }
-#pragma unroll 1
-            for (; s < ns; ++s) a0 = fma((JT)__ldg(m.spf + s * kSpStride + 3), sm.A[s * lda + k], a0);
-            sm.A[ns * lda + k] = -((a0 + a1) + (a2 + a3));
-        }
-        __syncwarp();
-    }
-#pragma unroll 1
-    for (int i = sl; i < n; i += G) sm.A[i * lda + i] += (JT)1;
-    if (f32) {
-        // solve for (delta rho, delta e / S), S = E_scale / rho: the energy
-        // row and column then sit on the species' scale, which keeps the
-        // FP32 elimination well conditioned
-        const JT S = to_jt<JT>(escale), iS = (JT)1 / S;
-#pragma unroll 1
-        for (int k = sl; k < ns; k += G) {
-            sm.A[ns * lda + k] *= iS;
-            sm.A[k * lda + ns] *= S;
-        }
-        if (sl == 0) sm.A[ns * lda + n] *= iS;
-    }
+    for (int i = sl; i < N; i += G) sm.A[i * ldA + i] += (JT)1;
     __syncwarp();
 
     // 7. Gaussian elimination with row partial pivoting on [A | -F]
@@ -860,13 +860,13 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     //    the diagonal
     bool sing = false;
 #pragma unroll 1
-    for (int j = 0; j < n; ++j) {
+    for (int j = 0; j < N; ++j) {
         unsigned long long best = 0;
-        int bi = n;
+        int bi = N;
 #pragma unroll 1
-        for (int i = j + sl; i < n; i += G) {
-            const unsigned long long kk = abs_key(sm.A[i * lda + j]);
-            if (bi == n || kk > best) {
+        for (int i = j + sl; i < N; i += G) {
+            const unsigned long long kk = abs_key(sm.A[i * ldA + j]);
+            if (bi == N || kk > best) {
                 best = kk;
                 bi = i;
             }
@@ -876,37 +876,37 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         else
             Grp<G>::argmax(best, bi);
         if (best == 0 || key_is_inf(best, JT(0))) sing = true;
-        if (bi != j && bi < n) {
+        if (bi != j && bi < N) {
 #pragma unroll 1
-            for (int k = j + sl; k <= n; k += G) {
-                const JT t = sm.A[j * lda + k];
-                sm.A[j * lda + k] = sm.A[bi * lda + k];
-                sm.A[bi * lda + k] = t;
+            for (int k = j + sl; k <= N; k += G) {
+                const JT t = sm.A[j * ldA + k];
+                sm.A[j * ldA + k] = sm.A[bi * ldA + k];
+                sm.A[bi * ldA + k] = t;
             }
         }
         __syncwarp();
         // (the FP64 pivot takes the full-precision reciprocal: a 1e-14 error
         // in every multiplier reaches the trace species of ill-conditioned
         // cells at 1e-10)
-        const JT inv = frcp(sm.A[j * lda + j]);
+        const JT inv = frcp(sm.A[j * ldA + j]);
         if (!f32) {
 #pragma unroll 1
-            for (int i = j + 1 + sl; i < n; i += G) sm.A[i * lda + j] *= inv;
+            for (int i = j + 1 + sl; i < N; i += G) sm.A[i * ldA + j] *= inv;
             __syncwarp();
-            if (sl == 0) sm.A[j * lda + j] = inv;
+            if (sl == 0) sm.A[j * ldA + j] = inv;
         }
         if (f32) {
             // FP32: bound by issue and latency, not by the pipe; the update
             // reads column j unscaled and never A[j][j]
-            lu_update_by_columns<G, JT>(sm.A, lda, n, j, sl, inv);
+            lu_update_by_columns<G, JT>(sm.A, ldA, N, j, sl, inv);
         } else {
             // FP64: a flat walk over the trailing elements keeps every lane of
             // every FP64 instruction busy (a masked lane costs a full slot)
             // (sl / cols and G / cols by a reciprocal multiply: both numerators
             // are below 64, and an integer division would take conversions on
             // the FP64 pipe)
-            const int cols = n - j;
-            const int tot = (n - j - 1) * cols;
+            const int cols = N - j;
+            const int tot = (N - j - 1) * cols;
             const unsigned rc = __ldg(m.div16 + cols);
             int e = sl;
             const int q0 = (int)(((unsigned)sl * rc) >> 16), dq = (int)(((unsigned)G * rc) >> 16);
@@ -914,10 +914,10 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             const int di = dq, dk = G - dq * cols;
 #pragma unroll 1
             for (; e < tot; e += G) {
-                sm.A[i * lda + k] -= sm.A[i * lda + j] * sm.A[j * lda + k];
+                sm.A[i * ldA + k] -= sm.A[i * ldA + j] * sm.A[j * ldA + k];
                 i += di;
                 k += dk;
-                if (k > n) {
+                if (k > N) {
                     k -= cols;
                     ++i;
                 }
@@ -925,17 +925,17 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         }
         __syncwarp();
         // FP32: the reciprocal replaces the pivot once every lane has read it
-        if (f32 && sl == 0) sm.A[j * lda + j] = inv;
+        if (f32 && sl == 0) sm.A[j * ldA + j] = inv;
     }
     __syncwarp();
     // back substitution, U delta = y
 #pragma unroll 1
-    for (int j = n - 1; j >= 0; --j) {
-        const JT dj = sm.A[j * lda + n] * sm.A[j * lda + j];
+    for (int j = N - 1; j >= 0; --j) {
+        const JT dj = sm.A[j * ldA + N] * sm.A[j * ldA + j];
         __syncwarp();
-        if (sl == 0) sm.A[j * lda + n] = dj;
+        if (sl == 0) sm.A[j * ldA + N] = dj;
 #pragma unroll 1
-        for (int i = sl; i < j; i += G) sm.A[i * lda + n] -= sm.A[i * lda + j] * dj;
+        for (int i = sl; i < j; i += G) sm.A[i * ldA + N] -= sm.A[i * ldA + j] * dj;
         __syncwarp();
     }
 
@@ -945,24 +945,21 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     //    (the FP32 path takes the norm's ratios in FP32: they decide
     //    convergence, not the iterate)
     double nrm = 0.0, des = 0.0;
-    float nrmf = 0.f, desf = 0.f;
+    float nrmf = 0.f, desf = 0.f, sef = 0.f;
     int nonfinite = 0;
-    const float escf = f32 ? d2f_rz(escale) : 0.f;
 #pragma unroll 1
-    for (int i = sl; i < n; i += G) {
+    for (int i = sl; i < N; i += G) {
         float df = 0.f;
         double d;
         if (f32) {
-            df = (float)sm.A[i * lda + n];
-            if (i == ns) df *= escf;
+            df = (float)sm.A[i * ldA + N];
             d = f2d_alu(df);
+            desf -= (float)sm.esJ[i] * df;
+            sef = fmaf(__ldg(m.spf + i * kSpStride + 3), df, sef);
         } else {
             d = (double)sm.A[i * lda + n];
-        }
-        if (f32)
-            desf += i < ns ? -(float)sm.esJ[i] * df : df;
-        else
             des += i < ns ? -sm.es[i] * d : d;
+        }
         const double xi = sm.x[i] + d;
         sm.x[i] = xi;
         if (!finite_bits(xi)) nonfinite = 1;
@@ -976,6 +973,19 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         } else {
             const double ri = den > 0.0 ? fabs(d) * frcp1(den) : (d != 0.0 ? CUDART_INF : 0.0);
             nrm = fmax(nrm, ri);
+        }
+    }
+    if (f32) {
+        // the eliminated energy unknown: de = -R_E - e_f . drho
+        const double de = -RE - f2d_alu(Grp<G>::sum(sef));
+        if (sl == 0) {
+            const double xe = sm.x[ns] + de;
+            sm.x[ns] = xe;
+            if (!finite_bits(xe)) nonfinite = 1;
+            const float denf = d2f_rz(fma(rtol, fabs(xe), atol_e)), adf = fabsf(d2f_rz(de));
+            const float ri = denf > 0.f ? adf * __frcp_rn(denf) : (adf != 0.f ? CUDART_INF_F : 0.f);
+            nrmf = fmaxf(nrmf, ri);
+            desf += d2f_rz(de);
         }
     }
     if (f32)
@@ -993,10 +1003,11 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     T_pred = T + des * dTde;
 }
 
-// At most 6 warps per block and 112 registers per thread: 18 warps fit on an
-// SM when shared memory allows it (3 blocks of 6).
+// At most 10 warps per block and 102 registers per thread: 20 warps fit on
+// an SM when shared memory allows it (2 blocks of 10; the mixed path at 36
+// species, 11.3 KB per cell).
 template <int G, typename JT>
-__global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, StepOptions o, StepBatch b) {
+__global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, StepOptions o, StepBatch b) {
     extern __shared__ __align__(16) char smem[];
     constexpr int S = 32 / G;
     const int lane = threadIdx.x & 31;
@@ -1013,7 +1024,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, S
     int state = kFree;
     long long cell = -1;
     double T = 1500.0, T0 = 1500.0, Tin = CUDART_NAN, h = 0.0, norm_prev = CUDART_INF;
-    double atol_rho = 0.0, atol_e = 0.0, escale = 1.0;
+    double atol_rho = 0.0, atol_e = 0.0;
     int k = 0, level = 0, attempts = 0, iters = 0, subs = 0, fails = 0;
     long long t_units = 0;
     const long long total = 1LL << o.max_halvings;
@@ -1088,7 +1099,6 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, S
             if (loading) {
                 atol_rho = o.atol_rel * rt;
                 atol_e = o.atol_rel * es;
-                escale = es > 0.0 && rt > 0.0 ? es / rt : 1.0;
                 T = b.T_in ? b.T_in[cell] : 1500.0;
                 if (nonfin || !(rt > 0.0))
                     write_fail(kCellBadInput);
@@ -1177,7 +1187,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 3) be_kernel(DeviceMech m, S
         // one Newton iteration of Eq. 29 for every slot
         double norm = 0.0, T_pred = T;
         bool bad = false;
-        newton_iteration<G, JT>(m, tab, sm, sl, T, h, atol_rho, atol_e, o.rtol, escale, norm, bad, T_pred);
+        newton_iteration<G, JT>(m, tab, sm, sl, T, h, atol_rho, atol_e, o.rtol, norm, bad, T_pred);
         if (state == kNewtonReady) {
             // start the next temperature recovery from the linear prediction
             if (T_pred > kTlo && T_pred < kThi) T = T_pred;
