@@ -326,50 +326,38 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         t.d_c.push_back(e.cb);
         t.d_c.push_back(e.ce);
     }
-    // gather lists: J_sk gathers nu_rs M_s D_rk over the reactions r; the
-    // energy row J_ek = -sum_s e_f,s J_sk gathers -de_r D_rk with the
-    // reaction's formation-energy change de_r = sum_s nu_rs M_s e_f,s
-    std::vector<double> de(nr, 0.0);
-    for (int r = 0; r < nr; ++r)
-        for (int s = 0; s < ns; ++s) de[r] += net(r, s) * d->molar_mass[s] * ef[s];
+    // gather lists: J_sk gathers nu_rs M_s D_rk over the reactions r (the
+    // kernels eliminate the energy unknown, so no energy row is gathered)
     struct Term { int j; double c; int nu; };
-    std::vector<std::vector<Term>> lists((size_t)(ns + 1) * ns);
+    std::vector<std::vector<Term>> lists((size_t)ns * ns);
     for (int j = 0; j < t.nD; ++j) {
         const int r = ents[j].r, k = ents[j].k;
         for (int s = 0; s < ns; ++s) {
             const int v = net(r, s);
             if (v != 0) lists[(size_t)s * ns + k].push_back({j, v * d->molar_mass[s], v});
         }
-        if (de[r] != 0.0) lists[(size_t)ns * ns + k].push_back({j, -de[r], 0});
     }
-    // FP64 lists: every entry, longest list first.  FP32 lists: the species
-    // entries only (the FP32 kernel forms the energy row from the species
-    // rows), longest first.
+    // the species entries, longest list first; the FP64 kernel's lists
+    // carry the coefficients nu_rs M_s, the FP32 kernel's nu_rs (it
+    // multiplies by M_s once per entry)
     auto longer = [&](int a, int b) { return lists[a].size() > lists[b].size(); };
-    std::vector<int> order((ns + 1) * ns), order32(ns * ns);
-    for (int i = 0; i < (ns + 1) * ns; ++i) order[i] = i;
-    for (int i = 0; i < ns * ns; ++i) order32[i] = i;
+    std::vector<int> order(ns * ns);
+    for (int i = 0; i < ns * ns; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), longer);
-    std::stable_sort(order32.begin(), order32.end(), longer);
-    t.nJ = (ns + 1) * ns;
+    t.nJ = ns * ns;
     t.j_ptr.push_back(0);
+    t.j_ptr32.push_back(0);
     for (int idx : order) {
         const int s = idx / ns, k = idx % ns;
         t.j_sk.push_back((s << 8) | k);
+        t.j_sk32.push_back((s << 8) | k);
         for (const auto &tm : lists[idx]) {
             t.j_d.push_back(tm.j);
             t.j_c.push_back(tm.c);
-        }
-        t.j_ptr.push_back((int)t.j_d.size());
-    }
-    t.j_ptr32.push_back(0);
-    for (int idx : order32) {
-        const int s = idx / ns, k = idx % ns;
-        t.j_sk32.push_back((s << 8) | k);
-        for (const auto &tm : lists[idx]) {
             t.j_d32.push_back(tm.j);
             t.j_nu.push_back(tm.nu);
         }
+        t.j_ptr.push_back((int)t.j_d.size());
         t.j_ptr32.push_back((int)t.j_d32.size());
     }
     // species lists (reactions with nu_rs != 0) in chunks of kChunk
@@ -622,7 +610,7 @@ int configure(Handle *h, int prec, int G, int wpb_req, LaunchCfg &cfg) {
     const void *fn = prec == CHEM_MIXED ? be_kernel_mixed(G) : be_kernel_fp64(G);
     if (!fn) return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d not available", G);
     const int S = 32 / G;
-    const long long sb = slot_bytes_for(h->mech, prec == CHEM_MIXED ? 4 : 8);
+    const long long sb = slot_stride(h->mech, prec == CHEM_MIXED ? 4 : 8, G);
     int best_warps = 0;
     LaunchCfg best{};
     // the attribute is per function and shared by every handle: allow the

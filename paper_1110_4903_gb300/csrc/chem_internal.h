@@ -110,8 +110,7 @@ struct DeviceMech {
     int ns, nr;
     int ntb;                    // third-body reactions: the first ntb (internal order)
     int nD, nD_F, nD_B, nD_FB;  // group ends: [0,F) [F,B) [B,FB) [FB,nD)
-    int nJ;                     // Jacobian entries gathered by the FP64 kernel: ns*ns species,
-                                // ns energy row (the FP32 kernel gathers the ns*ns species)
+    int nJ;                     // Jacobian entries gathered: ns*ns (species rows and columns)
     int n_items;                // species-gather work items
     const double *thermo;       // [16][2][ns] (coefficient-major, above)
     const double *tmid;         // [ns] (positive: compared as integers)
@@ -167,9 +166,10 @@ constexpr int kBlockHeaderBytes = 0;
 
 // Bytes of one cell slot, in this order (jt = sizeof of the Jacobian type):
 //   doubles   x, x0 (n each); FP64 path also es (ns)
-//   JT        FP64 path: dTdr (ns), w, u (ns+1 each: the species rows' T
-//             derivative and third-body vectors, then the energy row's), rhs (n)
-//             FP32 path: w, u, es (ns each), rhs (n)
+//   JT        FP64 path: dTdr, w, u, rhs (ns each: the reduced system's
+//             temperature column factor, the T-derivative and third-body
+//             vectors, the right-hand side)
+//             FP32 path: w, u, es, rhs (ns each)
 //   D region  first Q (nr doubles) and the species-gather partial sums (per
 //             item: sum nu Q in FP64, then sum nu dQ/dT and sum nu q_tb in JT),
 //             which are dead once the D entries (nD in JT) are written
@@ -177,9 +177,8 @@ constexpr int kBlockHeaderBytes = 0;
 //             values with a sentinel (ns+1 each) c, em, emi (doubles), FP64
 //             path hRT (double), ek (int), FP32 path cJ, hJ (float), then the
 //             per-reaction values dQdT, A1, A2 (nr JT each) and qtb (ntb JT);
-//             after the D entries: the augmented matrix in JT, n x (n+1) on
-//             the FP64 path, ns x (ns+1) on the FP32 path (energy unknown
-//             eliminated)
+//             after the D entries: the augmented matrix ns x (ns+1) in JT
+//             (the energy unknown is eliminated)
 __host__ __device__ inline long long align16(long long b) { return (b + 15) / 16 * 16; }
 
 #ifdef __CUDACC__
@@ -201,9 +200,7 @@ __host__ __device__ inline long long slot_dbl_bytes(int ns, int jt) {
     return align16((2LL * n + (jt == 8 ? ns : 0)) * 8);
 }
 __host__ __device__ inline long long slot_small_bytes(int ns, int jt) {
-    const int n = ns + 1;
-    const long long cnt = jt == 8 ? (long long)ns + 2LL * (ns + 1) + n : 3LL * ns + n;
-    return align16(cnt * jt);
+    return align16(4LL * ns * jt);
 }
 // species part of the union: c, em, emi (+ hRT) doubles, ek ints (+ cJ, hJ
 // floats), padded to 16 bytes so the per-reaction arrays that follow are
@@ -219,14 +216,24 @@ __host__ __device__ inline long long slot_dreg_bytes(int nr, int nD, int n_items
 }
 __host__ __device__ inline long long slot_union_bytes(int ns, int nr, int ntb, int jt) {
     const int n = ns + 1;
-    const int N = jt == 8 ? n : ns;
     const long long a = slot_union_species_bytes(ns, jt) + 3LL * nr * jt + (long long)ntb * jt,
-                    b = (long long)N * (N + 1) * jt;
+                    b = (long long)ns * n * jt;
     return align16(a > b ? a : b);
 }
 __host__ __device__ inline long long slot_bytes_for(const DeviceMech &m, int jt) {
     return slot_dbl_bytes(m.ns, jt) + slot_small_bytes(m.ns, jt) + slot_dreg_bytes(m.nr, m.nD, m.n_items, jt) +
            slot_union_bytes(m.ns, m.nr, m.ntb, jt);
+}
+// Stride between the cell slots of a block.  With several slots per warp
+// (lanes per cell below 32) the slots' equal offsets must fall in different
+// shared-memory banks, so the stride is an odd multiple of 16 bytes: the
+// S = 32 / G slots of a warp then start in S distinct 16-byte bank groups
+// (S <= 8).  A stride that is a multiple of 128 bytes put all eight slots
+// of a 4-lane warp in the same banks and cost the 9-species mixed path 20 %.
+__host__ __device__ inline long long slot_stride(const DeviceMech &m, int jt, int G) {
+    long long b = slot_bytes_for(m, jt);
+    if (G < 32 && ((b >> 4) & 1) == 0) b += 16;
+    return b;
 }
 
 }  // namespace chem

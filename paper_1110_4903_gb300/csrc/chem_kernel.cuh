@@ -19,11 +19,12 @@
 //   - pivot searches, range choices and finiteness tests compare integer
 //     keys; reciprocals refine rcp.approx; exp is a short table-driven
 //     evaluation, and the temperature recovery a multiplied-out polynomial.
-// The mixed path (JT = float) keeps the FP64 residual, rates, sources and
+// Both paths eliminate the energy unknown through the conservation of total
+// energy, so the elimination runs on the ns species unknowns.  The mixed
+// path (JT = float) keeps the FP64 residual, rates, sources and
 // temperature, and moves everything that only feeds the Jacobian to FP32;
-// it eliminates the energy unknown through the conservation of total
-// energy, and its LU is organised by columns.  It is bound by latency, so
-// its slot layout is cut to what it reads (20 warps per SM at 36 species).
+// its LU is organised by columns.  It is bound by latency, so its slot
+// layout is cut to what it reads (20 warps per SM at 36 species).
 //   Code size: with 20 warps at different phases, the instructions of one
 // Newton iteration have to stay in the SM's instruction caches.  The
 // compiler's unrolling of the many short runtime-count loops made the mixed
@@ -412,7 +413,7 @@ struct SlotMem {
     int *ek;
     JT *D, *dTdr, *w, *u, *A, *dQdT, *qtb, *A1, *A2, *rhs;
     JT *cJ, *hJ, *esJ;   // FP32 path: c, h/RT and e^sens in the Jacobian type
-    // layout and sizes in chem_internal.h (slot_bytes_for); the FP64 path has
+    // layout and sizes in chem_internal.h (slot_bytes_for, slot_stride); the FP64 path has
     // no FP32 copies (cJ = c, hJ = hRT), the FP32 path no FP64 hRT, es or
     // dTdr.  The species values of the rates (c, the split exponentials em,
     // emi, ek, and h/RT) share the union with the matrix: they are written
@@ -426,18 +427,15 @@ struct SlotMem {
         es = jt == 8 ? x0 + n : nullptr;
         char *q = base + slot_dbl_bytes(ns, jt);
         JT *t = reinterpret_cast<JT *>(q);
+        w = t;
+        u = w + ns;
+        rhs = u + ns;
         if (jt == 8) {
-            dTdr = t;
-            w = dTdr + ns;
-            u = w + ns + 1;
-            rhs = u + ns + 1;
+            dTdr = rhs + ns;
             esJ = reinterpret_cast<JT *>(es);
         } else {
             dTdr = nullptr;
-            w = t;
-            u = w + ns;
-            esJ = u + ns;
-            rhs = esJ + ns;
+            esJ = rhs + ns;
         }
         q += slot_small_bytes(ns, jt);
         // D region: Q and the gather partials until the D entries replace them
@@ -474,11 +472,11 @@ template <int G, typename JT>
 __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem<JT> &sm, int sl,
                                  double T, double h, double atol_rho, double atol_e, double rtol,
                                  double &norm, bool &bad, double &T_pred) {
-    const int ns = m.ns, nr = m.nr, n = ns + 1, lda = n + 1;
+    const int ns = m.ns, nr = m.nr;
     constexpr bool f32 = sizeof(JT) == 4;
-    // the linear system solved: FP64 the full (n) x (n) one; FP32 the
-    // species block with the energy unknown eliminated (phase 5)
-    const int N = f32 ? ns : n, ldA = N + 1;
+    // the linear system solved: the species block, with the energy unknown
+    // eliminated (phase 5)
+    const int N = ns, ldA = N + 1;
     const double invT = frcp(T);
     const double lnT = log(T);
     const double lnPaRT = log(kPa / kR) - lnT;
@@ -551,7 +549,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         rhocv = Grp<G>::sum(rhocv);
         dTde = frcp(rhocv);
 #pragma unroll 1
-        for (int s = sl; s < ns; s += G) sm.dTdr[s] = (JT)(-sm.es[s] * dTde);
+        for (int s = sl; s < ns; s += G) sm.dTdr[s] = (JT)(-(sm.es[s] + __ldg(m.sp + s * kSpStride + 3)) * dTde);
     }
     __syncwarp();
 
@@ -661,8 +659,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         pj[1] = squ;
     }
     __syncwarp();
-    double wde = 0.0, dEt = 0.0;
-    JT We = 0, Ue = 0;
+    double dEt = 0.0;
 #pragma unroll 1
     for (int s = sl; s < ns; s += G) {
         double sq = 0.0;
@@ -679,7 +676,6 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const double M = __ldg(m.sp + s * kSpStride);
         const double ef = __ldg(m.sp + s * kSpStride + 3);
         const JT MJ = f32 ? (JT)__ldg(m.spf + s * kSpStride) : (JT)M;
-        const JT efJ = f32 ? (JT)__ldg(m.spf + s * kSpStride + 3) : (JT)ef;
         const double wds = M * sq;
         // right-hand side -F_s = -(x_s - x0_s - h wdot_s), FP64 until stored
         const double dx = sm.x[s] - sm.x0[s];
@@ -687,33 +683,12 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const JT ws = MJ * sdq, us = MJ * squ;
         sm.w[s] = ws;
         sm.u[s] = us;
-        if (f32) {
-            dEt = fma(ef, dx, dEt);
-        } else {
-            wde -= ef * wds;
-            We += efJ * ws;
-            Ue += efJ * us;
-        }
+        dEt = fma(ef, dx, dEt);
     }
-    // FP32 path: the total-energy residual R_E = F_e + sum_s e_f,s F_s =
-    // (x_e - x0_e) + sum_s e_f,s (x_s - x0_s), in which the sources cancel
-    // (Omega_e = -sum_s e_f,s wdot_s); it replaces the energy equation
-    double RE = 0.0;
-    if (f32) {
-        RE = Grp<G>::sum(dEt) + (sm.x[ns] - sm.x0[ns]);
-    } else {
-        wde = Grp<G>::sum(wde);
-        if (sl == 0) sm.rhs[ns] = to_jt<JT>(-(sm.x[ns] - sm.x0[ns] - h * wde));
-    }
-    if (!f32) {
-        // the energy row's rank-one parts: J_ek = -sum_s e_f,s J_sk
-        We = Grp<G>::sum(We);
-        Ue = Grp<G>::sum(Ue);
-        if (sl == 0) {
-            sm.w[ns] = -We;
-            sm.u[ns] = -Ue;
-        }
-    }
+    // the total-energy residual R_E = F_e + sum_s e_f,s F_s = (x_e - x0_e) +
+    // sum_s e_f,s (x_s - x0_s), in which the sources cancel (Omega_e =
+    // -sum_s e_f,s wdot_s); it replaces the energy equation (phase 5)
+    const double RE = Grp<G>::sum(dEt) + (sm.x[ns] - sm.x0[ns]);
     __syncwarp();
 
     // 4. D entries: d Q_r / d rho_k without the all-ones third-body part,
@@ -773,44 +748,40 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     __syncwarp();
     // the per-reaction arrays are dead from here on; the matrix takes their place
 
-    // 5. right-hand side into the matrix.  FP64: -F = -(x - x0 - h Omega(x)).
-    //    FP32: the energy unknown is eliminated.  The energy row of I - hJ
-    //    is [e_f, 1] - sum_s e_f,s (row s) (J_ek = -sum_s e_f,s J_sk), so
-    //    with the species equations it reduces to the conservation law
-    //    de = -R_E - e_f . drho; substituted into the species rows, whose
-    //    energy-column entry is a_s = -h w_s dT/de, it leaves
+    // 5. right-hand side into the matrix, with the energy unknown
+    //    eliminated.  The energy row of I - hJ is [e_f, 1] - sum_s e_f,s
+    //    (row s) (J_ek = -sum_s e_f,s J_sk), so with the species equations
+    //    it reduces to the conservation law de = -R_E - e_f . drho;
+    //    substituted into the species rows, whose energy-column entry is
+    //    a_s = -h w_s dT/de, it leaves
     //      sum_k (A_sk - a_s e_f,k) drho_k = -F_s + a_s R_E,
-    //    the same solution as the full system in exact arithmetic, with one
-    //    unknown fewer and no energy row to form or scale
+    //    the same solution as the full system of Eq. 29 in exact
+    //    arithmetic, with one unknown fewer and no energy row to form
     const JT mh = to_jt<JT>(-h);
-    if (f32) {
-        const JT cRE = mh * (JT)dTdef * d2f_rz(RE);
+    {
+        const JT cRE = f32 ? mh * (JT)dTdef * d2f_rz(RE) : (JT)(-h * dTde * RE);
 #pragma unroll 1
         for (int i = sl; i < N; i += G) sm.A[i * ldA + N] = fma(sm.w[i], cRE, sm.rhs[i]);
-    } else {
-#pragma unroll 1
-        for (int i = sl; i < n; i += G) sm.A[i * lda + n] = sm.rhs[i];
     }
 
-    // 6. species and energy rows of -h J, density columns (longest gather
-    //    lists first, so the lanes of a pass run lists of nearly equal
-    //    length), then the temperature column
-    //    (four terms in flight per trip, two accumulators)
+    // 6. the reduced system's -h J'_sk = -h (J_sk - w_s e_f,k dT/de)
+    //    (longest gather lists first, so the lanes of a pass run lists of
+    //    nearly equal length; four terms in flight per trip, two
+    //    accumulators)
     const JT *__restrict__ Dv = sm.D;
 #pragma unroll 1
-    for (int p = sl; p < (f32 ? ns * ns : m.nJ); p += G) {
+    for (int p = sl; p < m.nJ; p += G) {
         const int2 meta = __ldg((f32 ? gl.j_meta32 : gl.j_meta) + p);
         const int len = meta.y >> 16;
         const int s = (meta.y >> 8) & 0xff, k = meta.y & 0xff;
         const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
-        // (FP32: the reduced system's column k: dT/drho_k - e_f,k dT/de)
+        // (the reduced system's column k: dT/drho_k - e_f,k dT/de)
         const JT dTdrk = f32 ? -(sm.esJ[k] + (JT)__ldg(m.spf + k * kSpStride + 3)) * (JT)dTdef : sm.dTdr[k];
         JT J = sm.w[s] * dTdrk + sm.u[s] * invMk;
         JT a0 = 0, a1 = 0;
         int e = meta.x, q = 0;
         if (f32) {
-            // species row: M_s sum nu_rs D_rk (the energy row follows from
-            // the species rows below)
+            // M_s sum nu_rs D_rk
             auto coef = [](unsigned wv) -> JT { return (JT)small_int_to_float((int)wv >> 24); };
 #pragma unroll 1
             for (; q + 4 <= len; q += 4, e += 4 * G) {
@@ -845,10 +816,6 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             J += a0 + a1;
         }
         sm.A[s * ldA + k] = mh * J;
-    }
-    if (!f32) {
-#pragma unroll 1
-        for (int s = sl; s < n; s += G) sm.A[s * lda + ns] = mh * (sm.w[s] * (JT)dTde);
     }
     __syncwarp();
 #pragma unroll 1
@@ -944,7 +911,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     //    next recovery's starting guess
     //    (the FP32 path takes the norm's ratios in FP32: they decide
     //    convergence, not the iterate)
-    double nrm = 0.0, des = 0.0;
+    double nrm = 0.0, des = 0.0, se = 0.0;
     float nrmf = 0.f, desf = 0.f, sef = 0.f;
     int nonfinite = 0;
 #pragma unroll 1
@@ -957,14 +924,14 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             desf -= (float)sm.esJ[i] * df;
             sef = fmaf(__ldg(m.spf + i * kSpStride + 3), df, sef);
         } else {
-            d = (double)sm.A[i * lda + n];
-            des += i < ns ? -sm.es[i] * d : d;
+            d = (double)sm.A[i * ldA + N];
+            des -= sm.es[i] * d;
+            se = fma(__ldg(m.sp + i * kSpStride + 3), d, se);
         }
         const double xi = sm.x[i] + d;
         sm.x[i] = xi;
         if (!finite_bits(xi)) nonfinite = 1;
-        const double at = i < ns ? atol_rho : atol_e;
-        const double den = fma(rtol, fabs(xi), at);
+        const double den = fma(rtol, fabs(xi), atol_rho);
         // a zero scale counts a nonzero update as infinitely large
         if (f32) {
             const float denf = d2f_rz(den), adf = fabsf(df);
@@ -975,17 +942,24 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             nrm = fmax(nrm, ri);
         }
     }
-    if (f32) {
+    {
         // the eliminated energy unknown: de = -R_E - e_f . drho
-        const double de = -RE - f2d_alu(Grp<G>::sum(sef));
+        const double de = -RE - (f32 ? f2d_alu(Grp<G>::sum(sef)) : Grp<G>::sum(se));
         if (sl == 0) {
             const double xe = sm.x[ns] + de;
             sm.x[ns] = xe;
             if (!finite_bits(xe)) nonfinite = 1;
-            const float denf = d2f_rz(fma(rtol, fabs(xe), atol_e)), adf = fabsf(d2f_rz(de));
-            const float ri = denf > 0.f ? adf * __frcp_rn(denf) : (adf != 0.f ? CUDART_INF_F : 0.f);
-            nrmf = fmaxf(nrmf, ri);
-            desf += d2f_rz(de);
+            const double den = fma(rtol, fabs(xe), atol_e);
+            if (f32) {
+                const float denf = d2f_rz(den), adf = fabsf(d2f_rz(de));
+                const float ri = denf > 0.f ? adf * __frcp_rn(denf) : (adf != 0.f ? CUDART_INF_F : 0.f);
+                nrmf = fmaxf(nrmf, ri);
+                desf += d2f_rz(de);
+            } else {
+                const double ri = den > 0.0 ? fabs(de) * frcp1(den) : (de != 0.0 ? CUDART_INF : 0.0);
+                nrm = fmax(nrm, ri);
+                des += de;
+            }
         }
     }
     if (f32)
@@ -1016,7 +990,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
     const int sl = lane - slot * G;
     const int ns = m.ns, n = ns + 1;
     const double *tab = m.exp_tab;   // 2 KB, stays in L1
-    const long long sbytes = slot_bytes_for(m, (int)sizeof(JT));
+    const long long sbytes = slot_stride(m, (int)sizeof(JT), G);
     SlotMem<JT> sm;
     sm.carve(smem + (size_t)(warp * S + slot) * sbytes, m);
     __syncthreads();
