@@ -48,7 +48,15 @@ def work_model(mech):
     mixed-precision path keeps in FP64 and the parts it moves to FP32: the
     Jacobian and LU, the heat capacities (they feed only dT/drho, dT/de and
     the next temperature guess), the temperature recovery's derivative and
-    the convergence-norm ratios.  All of it is FP64 on the FP64 path."""
+    the convergence-norm ratios.  All of it is FP64 on the FP64 path.
+
+    This counts the method as written (two exponentials per reaction for
+    K_f and K_b, Gaussian elimination on the N_s + 1 unknowns of Eq. 29).
+    The kernels do less for the same result: K_b comes from per-species
+    exponentials (one exp per reaction plus one per species), and the energy
+    unknown is eliminated through total-energy conservation (N_s unknowns).
+    The roofline fraction is therefore the method's work rate against the
+    FP64-pipe peak; the pipe's own utilisation is in the ncu counters."""
     ns, nr = mech.ns, mech.nr
     n = ns + 1
     nu = np.zeros((nr, ns), np.int64)
@@ -461,7 +469,9 @@ def main():
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe, the "
                                "binding pipe); probe measured 1.193 TFLOP/s",
                 "work_model": "%d FP64 flop per Newton iteration%s (exp counted as %d), %d Newton "
-                              "iterations per launch" % (
+                              "iterations per launch; algorithmic count of the method (two exp per "
+                              "reaction, elimination on N_s+1 unknowns), the kernel evaluates one "
+                              "exp per reaction plus one per species and eliminates N_s unknowns" % (
                                   wm["flops"] if name == "fp64" else wm["mixed_fp64"],
                                   "" if name == "fp64" else " plus %d FP32 flop" % wm["mixed_fp32"],
                                   EXP_FLOPS, it),
