@@ -337,6 +337,16 @@ int chem_batched_solve(int32_t method, int32_t n, int64_t n_sys, double *A, doub
 int chem_selftest_math(int64_t n, const double *x, double *y_exp, double *y_exp_ref,
                        double *y_rcp, double *y_rcp_ref, void *stream);
 
+/* Diagnostics for the equilibrium constants' exponent arithmetic (Eq. 24 as
+ * the kernels form it): at n device points, exp(x[i]) split into a mantissa
+ * y_mant[i] in [0.99, 2.01] and a power of two y_pow[i] (|x| >= 1024 and
+ * infinities saturate the power at +-4096 with mantissa 1; NaN gives a NaN
+ * mantissa), and y_scaled[i] = v[i] 2^k[i] on the exponent bits (zero,
+ * subnormal, infinite and NaN v unchanged; results below the normal range
+ * are signed zeros, above it infinities).  Synchronous. */
+int chem_selftest_scaled_exp(int64_t n, const double *x, double *y_mant, int32_t *y_pow,
+                             const double *v, const int32_t *k, double *y_scaled, void *stream);
+
 /* Human-readable text for a CHEM_E_* code (static storage). */
 const char *chem_strerror(int code);
 

@@ -1,5 +1,6 @@
 // chem_selftest.cu -- diagnostics: the step kernel's own exp and reciprocal
-// evaluated next to CUDA's, so tests can bound their error.
+// evaluated next to CUDA's, and its split exponential and power-of-two
+// scaling, so tests can bound their error and check their range handling.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -22,9 +23,50 @@ __global__ void selftest_kernel(long long n, const double *x, const double *tab_
     y_rcp_ref[i] = 1.0 / v;
 }
 
+__global__ void selftest_scaled_exp_kernel(long long n, const double *x, const double *tab, double *y_mant,
+                                           int *y_pow, const double *v, const int *k, double *y_scaled) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double y;
+    int p;
+    split_exp(x[i], tab, y, p);
+    y_mant[i] = y;
+    y_pow[i] = p;
+    y_scaled[i] = scale_pow2(v[i], k[i]);
+}
+
 }  // namespace chem
 
 using namespace chem;
+
+static int upload_exp_table(double **d_tab) {
+    std::vector<double> tab(kExpTab);
+    for (int j = 0; j < kExpTab; ++j) tab[j] = (double)std::exp2l((long double)j / kExpTab);
+    cudaError_t ce = cudaMalloc(d_tab, sizeof(double) * kExpTab);
+    if (ce != cudaSuccess) return fail(CHEM_E_OOM, "self-test table");
+    ce = cudaMemcpy(*d_tab, tab.data(), sizeof(double) * kExpTab, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        cudaFree(*d_tab);
+        return cuda_fail(ce, "self-test table");
+    }
+    return CHEM_OK;
+}
+
+extern "C" int chem_selftest_scaled_exp(int64_t n, const double *x, double *y_mant, int32_t *y_pow, const double *v,
+                                        const int32_t *k, double *y_scaled, void *stream) {
+    if (n < 0 || !x || !y_mant || !y_pow || !v || !k || !y_scaled) return fail(CHEM_E_INVALID_ARG, "NULL argument");
+    if (n == 0) return CHEM_OK;
+    double *d_tab = nullptr;
+    int rc = upload_exp_table(&d_tab);
+    if (rc) return rc;
+    selftest_scaled_exp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        n, x, d_tab, y_mant, y_pow, v, k, y_scaled);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(d_tab);
+    if (ce != cudaSuccess) return cuda_fail(ce, "self-test");
+    return CHEM_OK;
+}
 
 extern "C" int chem_selftest_math(int64_t n, const double *x, double *y_exp, double *y_exp_ref, double *y_rcp,
                                   double *y_rcp_ref, void *stream) {

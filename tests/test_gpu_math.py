@@ -34,3 +34,64 @@ def test_exp_and_reciprocal():
     nz = np.isfinite(x) & (np.abs(x) > 1e-300)
     ulp_r = np.abs(re[nz] - rr[nz]) / np.spacing(np.abs(rr[nz]))
     assert ulp_r.max() <= 1.0
+
+
+def test_split_exponential_and_scaling():
+    """The equilibrium constants' exponent arithmetic: exp(x) = y 2^k with y
+    within 2 ulp of exp(x - k ln 2) (extended precision) on |x| < 512 and 3
+    ulp up to 1024 (a square there), the saturated forms beyond, and v 2^k
+    against ldexp with the stated flushes."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1110_4903_gb300 import chem
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(-1023.9, 1023.9, 200000), rng.uniform(-5, 5, 50000),
+                        np.array([0.0, -0.0, 511.99, -511.99, 512.0, -512.0, 1023.99, -1023.99,
+                                  1024.0, -1024.0, 5000.0, -5000.0, np.inf, -np.inf, np.nan])])
+    vals = np.concatenate([rng.uniform(1, 2, 100000) * 2.0 ** rng.integers(-1000, 1000, 100000),
+                           -rng.uniform(1, 2, 1000),
+                           np.array([0.0, -0.0, 5e-324, -1e-310, np.inf, -np.inf, np.nan, 1.0, 1.0, 1.0, 1.0])])
+    ks = np.concatenate([rng.integers(-2200, 2200, 100000), rng.integers(-60, 60, 1000),
+                         np.array([5, 5, 100, 3000, -4, 4, 1, 1023, 1024, -1022, -1023])]).astype(np.int32)
+    m = max(len(x), len(vals))
+    x = np.resize(x, m) if len(x) < m else x
+    vals = np.concatenate([vals, np.ones(m - len(vals))])
+    ks = np.concatenate([ks, np.zeros(m - len(ks), np.int32)])
+    dev = torch.device("cuda")
+    xd, vd = torch.tensor(x, device=dev), torch.tensor(vals, device=dev)
+    kd = torch.tensor(ks, device=dev)
+    ym, ys = torch.empty_like(xd), torch.empty_like(xd)
+    yp = torch.empty(m, dtype=torch.int32, device=dev)
+    rc = chem.lib().chem_selftest_scaled_exp(m, xd.data_ptr(), ym.data_ptr(), yp.data_ptr(), vd.data_ptr(),
+                                             kd.data_ptr(), ys.data_ptr(), None)
+    assert rc == 0
+    ym, yp, ys = ym.cpu().numpy(), yp.cpu().numpy(), ys.cpu().numpy()
+    # split exponential
+    inr = np.isfinite(x) & (np.abs(x) < 1024)
+    assert np.all((ym[inr] >= 0.99) & (ym[inr] <= 2.01))
+    ld = np.longdouble
+    ref = np.exp(x[inr].astype(ld) - yp[inr].astype(ld) * np.log(ld(2)))
+    ulp = np.abs(ym[inr].astype(ld) - ref) / np.spacing(ref.astype(np.float64)).astype(ld)
+    half = np.abs(x[inr]) < 512          # beyond 512 the mantissa is the square of exp(x/2)'s
+    assert float(ulp[half].max()) <= 2.0, float(ulp[half].max())
+    assert float(ulp[~half].max()) <= 3.0, float(ulp[~half].max())
+    out = np.isfinite(x) & (np.abs(x) >= 1024) | np.isinf(x)
+    assert np.all(ym[out] == 1.0) and np.all(np.abs(yp[out]) == 4096)
+    assert np.all(np.sign(yp[out]) == np.sign(x[out]))
+    assert np.isnan(ym[np.isnan(x)]).all()
+    # power-of-two scaling
+    tiny = np.finfo(np.float64).tiny
+    normal = np.isfinite(vals) & (np.abs(vals) >= tiny)
+    with np.errstate(over="ignore", under="ignore"):
+        ref = np.ldexp(vals, ks)
+    ok = normal & (np.abs(ref) >= tiny) & np.isfinite(ref)
+    assert np.array_equal(ys[ok], ref[ok])
+    under = normal & (np.abs(ref) < tiny)
+    assert np.all(ys[under] == 0.0) and np.array_equal(np.signbit(ys[under]), np.signbit(vals[under]))
+    over = normal & ~np.isfinite(ref)
+    assert np.all(np.isinf(ys[over])) and np.array_equal(np.sign(ys[over]), np.sign(vals[over]))
+    keep = ~normal
+    assert np.array_equal(ys[keep], vals[keep], equal_nan=True)
