@@ -339,8 +339,8 @@ int chem_selftest_math(int64_t n, const double *x, double *y_exp, double *y_exp_
 
 /* Diagnostics for the equilibrium constants' exponent arithmetic (Eq. 24 as
  * the kernels form it): at n device points, exp(x[i]) split into a mantissa
- * y_mant[i] in [0.99, 2.01] and a power of two y_pow[i] (|x| >= 1024 and
- * infinities saturate the power at +-4096 with mantissa 1; NaN gives a NaN
+ * y_mant[i] in [0.99, 2.01] and a power of two y_pow[i] (|x| >= 2^22 and
+ * infinities saturate the power at +-2^24 with mantissa 1; NaN gives a NaN
  * mantissa), and y_scaled[i] = v[i] 2^k[i] on the exponent bits (zero,
  * subnormal, infinite and NaN v unchanged; results below the normal range
  * are signed zeros, above it infinities).  Synchronous. */

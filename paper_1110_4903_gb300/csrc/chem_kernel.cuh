@@ -235,22 +235,18 @@ __device__ __forceinline__ double fexp(double x, const double *tab) {
 
 // exp(x) = y 2^k with y in [0.99, 2.01]: the reduction of fexp without its
 // final scaling, so that products of many exponentials can be formed
-// without overflow.  512 <= |x| < 1024 takes the square of exp(x/2);
-// beyond that (and for infinities) k saturates at +-4096 with y = 1, and
-// a NaN x gives a NaN y.
+// without overflow.  The reduction is exact up to its two roundings for
+// any |x| < 2^22 (the products with ln2/256 are fused, and the table index
+// fits an int); beyond that (and for infinities) k saturates at +-2^24 with
+// y = 1, and a NaN x gives a NaN y.
 __device__ __forceinline__ void split_exp(double x, const double *tab, double &y, int &k) {
     const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
     const unsigned ex = (hi >> 20) & 0x7ffu;
-    bool sq = false;
-    if (ex > 0x407u) {
-        if (ex > 0x408u) {
-            const bool nan = ex == 0x7ffu && ((hi & 0xfffffu) | (unsigned)__double_as_longlong(x));
-            y = nan ? x : 1.0;
-            k = (hi >> 31) ? -4096 : 4096;
-            return;
-        }
-        x *= 0.5;
-        sq = true;
+    if (ex >= 0x415u) {
+        const bool nan = ex == 0x7ffu && ((hi & 0xfffffu) | (unsigned)__double_as_longlong(x));
+        y = nan ? x : 1.0;
+        k = (hi >> 31) ? -(1 << 24) : (1 << 24);
+        return;
     }
     const double kShift = 6755399441055744.0;               // 1.5 * 2^52
     const double t = fma(x, 369.3299304675746, kShift);     // x * 256/ln2, rounded
@@ -265,10 +261,6 @@ __device__ __forceinline__ void split_exp(double x, const double *tab, double &y
     const double s = __ldg(tab + (n & (kExpTab - 1)));
     y = fma(s, p, s);
     k = n >> 8;
-    if (sq) {
-        y *= y;
-        k *= 2;
-    }
 }
 // v 2^k on the exponent bits for a normal v; zero, subnormal, infinite and
 // NaN v come back unchanged, a result below the normal range is a signed
