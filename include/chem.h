@@ -9,8 +9,10 @@
  * the energy e (Eq. 3, formation energy excluded) over one fluid time step
  * dt at constant volume, with the sources of Sec. 3.2 (Eqs. 23-27) and the
  * implicit system of Eq. 29 solved by Gaussian elimination.  Here Eq. 29 is
- * iterated to the full backward-Euler solution by Newton's method with
- * (N_s+1)x(N_s+1) LU with row partial pivoting, on substeps dt 2^-level.
+ * iterated to the full backward-Euler solution by Newton's method, on
+ * substeps dt 2^-level.  Each Newton system is reduced exactly to the N_s
+ * species unknowns (the energy unknown follows from the conservation of
+ * total energy) and solved by LU with row partial pivoting.
  *
  * Conventions
  *  - Units SI (kg, m, s, mol, K, J), except the Arrhenius factor A, given in

@@ -82,13 +82,14 @@ constexpr int kExpTab = 256;
 // sits at word base + q G + lane, where base is the pass's first word, so the
 // lanes of a pass read their q-th terms from consecutive words (one cache
 // line per warp load instead of one per lane).
-//   FP64 kernel: every Jacobian entry, longest list first
+//   The ns*ns species entries (the kernels eliminate the energy unknown, so
+//   no energy row is gathered), longest list first, in both forms:
 //     j_meta[p]   = {first word of entry p, k | s << 8 | terms << 16}
-//     j_d, j_c    = D index and coefficient nu_rs M_s (energy row: -de_r)
-//   FP32 kernel: the ns*ns species entries, longest list first (it forms the
-//   energy row from the species rows)
-//     j_meta32[p] = as j_meta
-//     j_w         = D index | nu_rs << 24 (the row's M_s multiplies the sum)
+//     j_d, j_c    = D index and coefficient nu_rs M_s (FP64 kernel)
+//     j_meta32[p] = as j_meta, with the FP32 lists' own word positions
+//     j_w         = D index | nu_rs << 24 (FP32 kernel: the row's M_s
+//                   multiplies the sum; terms ordered across the lanes of a
+//                   pass for distinct shared-memory banks)
 //   it_meta[i] = {first word of item i, entries}
 //   sp_w       = r | nu_rs << 24;  sp_nu = nu_rs (FP64)
 struct GatherLayout {
@@ -124,9 +125,9 @@ struct DeviceMech {
     const double *eff_c;        //        alpha - 1
     const int4 *d_pk;           // [nD]
     const double *d_c;          // [nD][3]
-    // Jacobian entries (s = ns: energy row), longest gather list first, and
-    // the species lists (reactions with nu_rs != 0) cut into items of at
-    // most kChunk entries; per-G layouts above
+    // Jacobian entries (species rows and columns), longest gather list
+    // first, and the species lists (reactions with nu_rs != 0) cut into
+    // items of at most kChunk entries; per-G layouts above
     GatherLayout gl[kLayouts];
     const int *sp_item_ptr;     // [ns+1] work items of each species
     const double *exp_tab;      // [kExpTab] 2^(j/kExpTab)
