@@ -164,11 +164,11 @@ static void third_body_first(const chem_mech_desc *in, ReorderedMech &o) {
 
 // Derived tables (layouts in chem_internal.h)
 struct HostTables {
-    std::vector<double> thermo, tmid, tpoly, sp, rxn_d, eff_c, d_c, j_c, sp_nu, exp_tab;
+    std::vector<double> thermo, tmid, tpoly, sp, rxn_d, eff_c, d_c, j_c, exp_tab;
     std::vector<unsigned> div16;
     std::vector<float> tpoly_f;
     std::vector<float> rxn_df, d_cef, spf;
-    std::vector<int4> d_pk;
+    std::vector<int2> d_pk;
     std::vector<unsigned> j_w, sp_w;
     std::vector<int> rxn_f, eff_ptr, eff_sp, d_i0, d_i1, j_sk, j_ptr, j_d, it_ptr, sp_item_ptr, sp_r;
     std::vector<int2> j_meta;
@@ -177,7 +177,7 @@ struct HostTables {
         std::vector<int2> j_meta, j_meta32, it_meta;
         std::vector<unsigned> j_w, sp_w;
         std::vector<int> j_d;
-        std::vector<double> j_c, sp_nu;
+        std::vector<double> j_c;
     } lay[kLayouts];
     int nD = 0, nD_F = 0, nD_B = 0, nD_FB = 0, nJ = 0, n_items = 0, ntb = 0;
 };
@@ -277,7 +277,7 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         t.eff_ptr[r + 1] = (int)t.eff_sp.size();
     }
     // D entries: (reaction, column species) pairs, grouped by kind
-    struct DEnt { int r, k, grp; int fa, fb, ba, bb; double cf, cb, ce; };
+    struct DEnt { int r, k, grp; int fa, fb, ba, bb, vf, vb; double cf, cb, ce, alpha1; };
     std::vector<DEnt> ents;
     for (int r = 0; r < nr; ++r) {
         std::vector<int> cols;
@@ -307,9 +307,12 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
             e.fa = e.fb = e.ba = e.bb = SENT;
             if (vf > 0) rest(facR[r], e.fa, e.fb);
             if (vb > 0) rest(facP[r], e.ba, e.bb);
+            e.vf = vf;
+            e.vb = vb;
             e.cf = vf * invM;
             e.cb = vb * invM;
-            e.ce = (tb ? (d->tb_eff ? d->tb_eff[(size_t)r * ns + k] : 1.0) - 1.0 : 0.0) * invM;
+            e.alpha1 = tb ? (d->tb_eff ? d->tb_eff[(size_t)r * ns + k] : 1.0) - 1.0 : 0.0;
+            e.ce = e.alpha1 * invM;
             e.grp = vf > 0 && vb == 0 ? 0 : (vf == 0 && vb > 0 ? 1 : (vf > 0 ? 2 : 3));
             ents.push_back(e);
         }
@@ -320,7 +323,8 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         if (e.grp <= 0) t.nD_F++;
         if (e.grp <= 1) t.nD_B++;
         if (e.grp <= 2) t.nD_FB++;
-        t.d_i0.push_back(e.r | (e.k << 16));
+        t.d_i0.push_back(e.r | (e.vf << 16) | (e.vb << 20));
+        t.d_cef.push_back((float)e.alpha1);
         t.d_i1.push_back(e.fa | (e.fb << 8) | (e.ba << 16) | (e.bb << 24));
         t.d_c.push_back(e.cf);
         t.d_c.push_back(e.cb);
@@ -369,7 +373,6 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
             const int v = net(r, s);
             if (v == 0) continue;
             t.sp_r.push_back(r);
-            t.sp_nu.push_back((double)v);
             t.sp_nui.push_back(v);
             if (++cnt == kChunk) {
                 t.it_ptr.push_back((int)t.sp_r.size());
@@ -393,15 +396,8 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         t.rxn_df[(size_t)r * kRxnDStride + 1] = (float)t.rxn_d[(size_t)r * kRxnDStride + 2];
         t.rxn_df[(size_t)r * kRxnDStride + 2] = (float)t.rxn_d[(size_t)r * kRxnDStride + 3];
     }
-    auto fbits = [](double c) {
-        const float f = (float)c;
-        int bits;
-        memcpy(&bits, &f, sizeof bits);
-        return bits;
-    };
     for (int j = 0; j < t.nD; ++j) {
-        t.d_pk.push_back(make_int4(t.d_i0[j], t.d_i1[j], fbits(t.d_c[3 * j]), fbits(t.d_c[3 * j + 1])));
-        t.d_cef.push_back((float)t.d_c[3 * j + 2]);
+        t.d_pk.push_back(make_int2(t.d_i0[j], t.d_i1[j]));
     }
     // a term's word: D index (or reaction) in bits 0..23, nu_rs in 24..31
     auto word = [](int i, int nu) { return (unsigned)i | ((unsigned)(nu & 0xff) << 24); };
@@ -487,10 +483,8 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         for (size_t e = 0; e < pos.size(); ++e) L.j_w[pos[e]] = t.j_w[e];
         const int ni = interleave(t.n_items, t.it_ptr, G, L.it_meta, pos, 0, nullptr);
         L.sp_w.assign(std::max(ni, 1), 0u);
-        L.sp_nu.assign(std::max(ni, 1), 0.0);
         for (size_t e = 0; e < pos.size(); ++e) {
             L.sp_w[pos[e]] = t.sp_w[e];
-            L.sp_nu[pos[e]] = t.sp_nu[e];
         }
         if (L.it_meta.empty()) L.it_meta.push_back(make_int2(0, 0));
     }
@@ -511,13 +505,13 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     // keep every array non-empty so device pointers are valid
     auto pad_f = [](std::vector<float> &v) { if (v.empty()) v.push_back(0.0f); };
     pad_f(t.rxn_df); pad_f(t.d_cef);
-    if (t.d_pk.empty()) t.d_pk.push_back(make_int4(0, 0, 0, 0));
+    if (t.d_pk.empty()) t.d_pk.push_back(make_int2(0, 0));
     auto pad_u = [](std::vector<unsigned> &v) { if (v.empty()) v.push_back(0u); };
     pad_u(t.j_w); pad_u(t.sp_w);
     auto pad_i = [](std::vector<int> &v) { if (v.empty()) v.push_back(0); };
     auto pad_d = [](std::vector<double> &v) { if (v.empty()) v.push_back(0.0); };
     pad_i(t.eff_sp); pad_d(t.eff_c); pad_d(t.d_c);
-    pad_i(t.j_d); pad_d(t.j_c); pad_d(t.sp_nu); pad_i(t.rxn_f); pad_d(t.rxn_d);
+    pad_i(t.j_d); pad_d(t.j_c); pad_i(t.rxn_f); pad_d(t.rxn_d);
 }
 
 // Copies the tables into one device allocation.
@@ -548,7 +542,6 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
         i_lay[li][3] = addv(L.j_c);
         i_lay[li][4] = addv(L.it_meta);
         i_lay[li][5] = addv(L.sp_w);
-        i_lay[li][6] = addv(L.sp_nu);
     }
     cudaError_t e = cudaMalloc(&h->dev_tables, total);
     if (e != cudaSuccess) return fail(CHEM_E_OOM, "device tables (%zu bytes): %s", total, cudaGetErrorString(e));
@@ -579,7 +572,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     m.eff_ptr = (const int *)at(i_ep);
     m.eff_sp = (const int *)at(i_es);
     m.eff_c = (const double *)at(i_ec);
-    m.d_pk = (const int4 *)at(i_dpk);
+    m.d_pk = (const int2 *)at(i_dpk);
     m.d_c = (const double *)at(i_dc);
     for (int li = 0; li < kLayouts; ++li) {
         GatherLayout &g = m.gl[li];
@@ -590,7 +583,6 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
         g.j_c = (const double *)at(i_lay[li][3]);
         g.it_meta = (const int2 *)at(i_lay[li][4]);
         g.sp_w = (const unsigned *)at(i_lay[li][5]);
-        g.sp_nu = (const double *)at(i_lay[li][6]);
     }
     m.sp_item_ptr = (const int *)at(i_sip);
 

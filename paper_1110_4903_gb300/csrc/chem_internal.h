@@ -71,12 +71,12 @@ constexpr int kExpTab = 256;
 // progress rate Q_r depends on, holding dQ_r/drho_k without the all-ones
 // third-body part.  They are sorted into four groups so each group is one
 // uniform loop: reactant-only, product-only, both sides, efficiency-only.
-//   d_pk = {r | k << 16,
+//   d_pk = {r | nu'_rk << 16 | nu''_rk << 20,
 //           fa | fb << 8 | ba << 16 | bb << 24  (the remaining factors of
-//                d(prod c)/dc_k on each side, sentinel ns if none),
-//           FP32 bits of nu'_rk / M_k, FP32 bits of nu''_rk / M_k}
-//   d_c  = {nu'_rk / M_k, nu''_rk / M_k, (alpha_rk - 1) / M_k} (FP64)
-//   d_cef = (alpha_rk - 1) / M_k (FP32)
+//                d(prod c)/dc_k on each side, sentinel ns if none)}
+//   d_c  = {nu'_rk / M_k, nu''_rk / M_k, (alpha_rk - 1) / M_k} (FP64 kernel)
+//   d_cef = alpha_rk - 1 (FP32 kernel, whose D entries are M_k dQ_r/drho_k:
+//           the 1/M_k is applied once per Jacobian entry in the gather)
 // Gather lists laid out for G lanes per cell.  List p (a Jacobian entry, or
 // an item of a species list) runs in pass p / G on lane p % G; its q-th term
 // sits at word base + q G + lane, where base is the pass's first word, so the
@@ -91,7 +91,7 @@ constexpr int kExpTab = 256;
 //                   multiplies the sum; terms ordered across the lanes of a
 //                   pass for distinct shared-memory banks)
 //   it_meta[i] = {first word of item i, entries}
-//   sp_w       = r | nu_rs << 24;  sp_nu = nu_rs (FP64)
+//   sp_w       = r | nu_rs << 24
 struct GatherLayout {
     const int2 *j_meta;
     const int2 *j_meta32;
@@ -100,7 +100,6 @@ struct GatherLayout {
     const double *j_c;
     const int2 *it_meta;
     const unsigned *sp_w;
-    const double *sp_nu;
 };
 constexpr int kLayouts = 5;   // G = 2, 4, 8, 16, 32
 __host__ __device__ constexpr int layout_index(int G) {
@@ -123,7 +122,7 @@ struct DeviceMech {
     const int *eff_ptr;         // [nr+1] CSR of efficiency corrections of +M reactions
     const int *eff_sp;          //        species
     const double *eff_c;        //        alpha - 1
-    const int4 *d_pk;           // [nD]
+    const int2 *d_pk;           // [nD]
     const double *d_c;          // [nD][3]
     // Jacobian entries (species rows and columns), longest gather list
     // first, and the species lists (reactions with nu_rs != 0) cut into
@@ -134,7 +133,7 @@ struct DeviceMech {
     const unsigned *div16;      // [67] ceil(2^16 / c): x / c = (x div16[c]) >> 16 for x < 64
     // FP32 copies for the mixed-precision Jacobian
     const float *rxn_df;        // [nr][4] beta, Ea/R, sum nu, 0
-    const float *d_cef;         // [nD] efficiency coefficient in FP32
+    const float *d_cef;         // [nD] alpha - 1 in FP32
     const float *spf;           // [ns][4] M, 1/M, R/M, e_f in FP32
 };
 

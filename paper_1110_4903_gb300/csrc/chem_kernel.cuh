@@ -207,6 +207,14 @@ static __device__ __noinline__ double exp_outside(double x) { return exp(x); }
 __device__ __forceinline__ float small_int_to_float(int v) {
     return __int_as_float(0x4B400000 + v) - 12582912.0f;
 }
+// A nonzero signed integer (|v| < 2^20) as a double from integer operations
+// only (sign, biased exponent of the top bit, the bits below it), exact.
+__device__ __forceinline__ double small_int_to_double(int v) {
+    const unsigned a = v < 0 ? (unsigned)-v : (unsigned)v;
+    const int e = 31 - __clz(a);
+    const unsigned hi = (v < 0 ? 0x80000000u : 0u) | ((unsigned)(1023 + e) << 20) | ((a << (20 - e)) & 0xfffffu);
+    return __hiloint2double((int)hi, 0);
+}
 
 // exp by the table-driven reduction of P. T. P. Tang, ACM TOMS 15(2), 1989:
 // x = (256 k + j) ln2/256 + r with |r| <= ln2/512, exp(x) = 2^k 2^(j/256) e^r,
@@ -637,7 +645,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
                 const int e = im.x + q * G;
                 const unsigned wv = __ldg(gl.sp_w + e);
                 const int r = (int)(wv & 0xffffffu);
-                const double nu = __ldg(gl.sp_nu + e);
+                const double nu = small_int_to_double((int)wv >> 24);   // nu_rs != 0 in a list
                 const JT nuj = f32 ? (JT)small_int_to_float((int)wv >> 24) : (JT)nu;
                 sq = fma(nu, sm.Q[r], sq);
                 sdq += nuj * sm.dQdT[r];
@@ -685,8 +693,9 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
 
     // 4. D entries: d Q_r / d rho_k without the all-ones third-body part,
     //    grouped so that each group is one uniform loop body (FP32: one
-    //    branch-free body that selects the sides by group, two entries per
-    //    trip so their loads overlap)
+    //    branch-free body that selects the sides by their orders, two
+    //    entries per trip so their loads overlap; its entries are M_k dQ_r /
+    //    drho_k, with integer orders, and the gather applies the 1/M_k)
     if (f32) {
         const JT *__restrict__ A1v = sm.A1;
         const JT *__restrict__ A2v = sm.A2;
@@ -694,13 +703,11 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const JT *__restrict__ qv = sm.qtb;
         JT *__restrict__ Dw = sm.D;
         auto dval = [&](int j) -> JT {
-            const int4 pk = __ldg(m.d_pk + j);
-            const int r = pk.x & 0xffff, i1 = pk.y;
-            const JT fwd = (JT)__int_as_float(pk.z) * A1v[r] * (cJv[i1 & 0xff] * cJv[(i1 >> 8) & 0xff]);
-            const JT bwd = (JT)__int_as_float(pk.w) * A2v[r] * (cJv[(i1 >> 16) & 0xff] * cJv[(i1 >> 24) & 0xff]);
-            const bool hasf = j < m.nD_F || (j >= m.nD_B && j < m.nD_FB);
-            const bool hasb = j >= m.nD_F && j < m.nD_FB;
-            JT d = (hasf ? fwd : (JT)0) - (hasb ? bwd : (JT)0);
+            const int2 pk = __ldg(m.d_pk + j);
+            const int r = pk.x & 0xffff, vf = (pk.x >> 16) & 15, vb = (pk.x >> 20) & 15, i1 = pk.y;
+            const JT fwd = (JT)small_int_to_float(vf) * A1v[r] * (cJv[i1 & 0xff] * cJv[(i1 >> 8) & 0xff]);
+            const JT bwd = (JT)small_int_to_float(vb) * A2v[r] * (cJv[(i1 >> 16) & 0xff] * cJv[(i1 >> 24) & 0xff]);
+            JT d = (vf ? fwd : (JT)0) - (vb ? bwd : (JT)0);
             if (r < m.ntb) d = fma((JT)__ldg(m.d_cef + j), qv[r], d);
             return d;
         };
@@ -715,7 +722,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     } else
 #pragma unroll 1
     for (int j = sl; j < m.nD; j += G) {
-        const int2 pk = __ldg(reinterpret_cast<const int2 *>(m.d_pk + j));
+        const int2 pk = __ldg(m.d_pk + j);
         const int i0 = pk.x, i1 = pk.y;
         const int r = i0 & 0xffff;
         const int fa = i1 & 0xff, fb = (i1 >> 8) & 0xff, ba = (i1 >> 16) & 0xff, bb = (i1 >> 24) & 0xff;
@@ -769,7 +776,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
         // (the reduced system's column k: dT/drho_k - e_f,k dT/de)
         const JT dTdrk = f32 ? -(sm.esJ[k] + (JT)__ldg(m.spf + k * kSpStride + 3)) * (JT)dTdef : sm.dTdr[k];
-        JT J = sm.w[s] * dTdrk + sm.u[s] * invMk;
+        JT J = f32 ? sm.w[s] * dTdrk : sm.w[s] * dTdrk + sm.u[s] * invMk;
         JT a0 = 0, a1 = 0;
         int e = meta.x, q = 0;
         if (f32) {
@@ -791,7 +798,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
                 const unsigned wv = __ldg(gl.j_w + e);
                 a0 = fma(coef(wv), Dv[wv & 0xffffffu], a0);
             }
-            J = fma((JT)__ldg(m.spf + s * kSpStride), a0 + a1, J);
+            // (D entries scaled by M_k: J_sk = w_s dT/drho_k + (u_s + M_s sum) / M_k)
+            J = fma(invMk, fma((JT)__ldg(m.spf + s * kSpStride), a0 + a1, sm.u[s]), J);
         } else {
 #pragma unroll 1
             for (; q + 4 <= len; q += 4, e += 4 * G) {
