@@ -37,7 +37,7 @@ EXP_FLOPS = 40          # one FP64 exp occupies the FP64 pipe like ~20 DFMA (mea
 # single-pass ncu capture of a full-size launch of the current kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum; part of the state written
 # back is still in L2 when the kernel ends).  Other workloads report null.
-MEASURED_TRAFFIC = {"mixed": None, "fp64": None}
+MEASURED_TRAFFIC = {"mixed": 79.99e6 + 31.74e6, "fp64": 80.14e6 + 35.78e6}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 x max clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FFMA/clk x 2 x max clock
 
