@@ -18,7 +18,9 @@
 //     path converts between FP64 and FP32 on the integer pipe;
 //   - pivot searches, range choices and finiteness tests compare integer
 //     keys; reciprocals refine rcp.approx; exp is a short table-driven
-//     evaluation, and the temperature recovery a multiplied-out polynomial.
+//     evaluation, once per reaction (K_f) and once per species (the split
+//     exponentials the equilibrium constants are multiplied from), and the
+//     temperature recovery a multiplied-out polynomial.
 // Both paths eliminate the energy unknown through the conservation of total
 // energy, so the elimination runs on the ns species unknowns.  The mixed
 // path (JT = float) keeps the FP64 residual, rates, sources and
