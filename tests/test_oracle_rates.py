@@ -129,3 +129,27 @@ def test_generated_mechanisms_are_element_balanced(gen_mechs):
                 if m.prod_sp[r, j] >= 0:
                     v += m.prod_nu[r, j] * m.elem_comp[m.prod_sp[r, j]]
             assert not v.any()
+
+
+def test_equilibrium_constants_as_products_over_factor_slots(oracle_mod):
+    # The kernels form 1/K_c (Eq. 24) as a product over the reaction's factor
+    # slots (species listed with repetition, up to three per side) of each
+    # product's exp(g/RT - ln(P_a/RT)) and each reactant's inverse: that is
+    # exp(dG/RT) (RT/P_a)^dnu because dnu is the number of product factors
+    # minus reactant factors, and a species on both sides cancels.
+    for mech in (synth.h2_air_9sp(), synth.hydrocarbon_36sp()):
+        om = oracle_mod.OracleMech(mech)
+        for T in (300.0, 800.0, 1500.0, 2800.0, 5000.0):
+            g = np.array([om.thermo(s, T)[1] - om.thermo(s, T)[2] for s in range(mech.ns)])
+            L = np.log(PA / (R * T))
+            _, Kc, _ = om.rate_constants(T)
+            for r in range(mech.nr):
+                ex = 0.0
+                for j in range(3):
+                    if mech.prod_sp[r, j] >= 0:
+                        ex += mech.prod_nu[r, j] * (g[mech.prod_sp[r, j]] - L)
+                    if mech.reac_sp[r, j] >= 0:
+                        ex -= mech.reac_nu[r, j] * (g[mech.reac_sp[r, j]] - L)
+                # the exponent sums terms of size |g| up to a few hundred
+                tol = 1e-15 * (np.abs(g).max() + abs(L)) * 8
+                assert abs(ex - np.log(1.0 / Kc[r])) <= tol, (mech.name, T, r)
