@@ -23,6 +23,7 @@ PA = 101325.0
 TREF = 298.15
 
 OK, NEWTON_FAILED, T_FAILED, BAD_INPUT, TOO_MANY_STEPS = 0, 1, 2, 3, 4
+REPLAY_NOT_CONVERGED, REPLAY_MISMATCH = 5, 6
 
 
 def build(force: bool = False) -> str:
@@ -92,6 +93,12 @@ def lib():
             L.om_default_opts.argtypes = [p]
             L.om_advance_cell.argtypes = [p, p, p, p, d, d, p]
             L.om_advance_batch.argtypes = [p, p, C.c_long, C.c_long, p, p, d, p, p, p, p, p, p]
+            L.om_advance_batch_sched.argtypes = [p, p, C.c_long, C.c_long, p, p, d, p, p, p, p, p,
+                                                 p, p, i]
+            L.om_advance_cell_sched.argtypes = [p, p, p, p, d, d, p, i, p]
+            L.om_advance_cell_replay.argtypes = [p, p, p, p, d, d, p, i, p]
+            L.om_advance_batch_replay.argtypes = [p, p, C.c_long, C.c_long, p, p, d, p, p, i, p,
+                                                  p, p, p]
             L.om_state_from_tpy.argtypes = [p, C.c_long, C.c_long, p, p, p, p, p]
             _lib = L
     return _lib
@@ -194,9 +201,70 @@ class OracleMech:
         return r, ev.value, dict(status=res.status, newton_iters=res.newton_iters,
                                  substeps=res.substeps, failures=res.failures, T=res.T)
 
-    def advance_batch(self, rho, e, dt, T_in=None, opts=None, threads=1):
+    def advance_cell_sched(self, rho, e, dt, T_guess=1500.0, opts=None, words=8):
+        """advance_cell that also returns the accepted-attempt bits (uint32
+        words: bit a set when substep attempt a was accepted)."""
+        o = opts if opts is not None else default_opts()
+        r = np.ascontiguousarray(rho, np.float64).copy()
+        ev = C.c_double(float(e))
+        sched = np.zeros(words, np.uint32)
+        res = _CellResult()
+        lib().om_advance_cell_sched(self.ref, C.byref(o), _ptr(r), C.byref(ev), float(dt),
+                                    float(T_guess), _ptr(sched), words, C.byref(res))
+        return r, ev.value, sched, dict(status=res.status, newton_iters=res.newton_iters,
+                                        substeps=res.substeps, failures=res.failures, T=res.T)
+
+    def advance_cell_replay(self, rho, e, dt, accepted, n_attempts, T_guess=1500.0, opts=None):
+        """One cell along the given schedule (om_advance_cell_replay)."""
+        o = opts if opts is not None else replay_opts()
+        r = np.ascontiguousarray(rho, np.float64).copy()
+        ev = C.c_double(float(e))
+        acc = np.ascontiguousarray(accepted, np.uint32)
+        res = _CellResult()
+        lib().om_advance_cell_replay(self.ref, C.byref(o), _ptr(r), C.byref(ev), float(dt),
+                                     float(T_guess), _ptr(acc), int(n_attempts), C.byref(res))
+        return r, ev.value, dict(status=res.status, newton_iters=res.newton_iters,
+                                 substeps=res.substeps, failures=res.failures, T=res.T)
+
+    def advance_batch_replay(self, rho, e, dt, accepted, n_attempts, T_in=None, opts=None,
+                             threads=1):
+        """The replay over a batch: accepted [n, words] uint32, n_attempts [n].
+        Returns new rho, e and dict(T, status, newton_iters)."""
+        o = opts if opts is not None else replay_opts()
+        rho = np.ascontiguousarray(rho, np.float64).copy()
+        e = np.ascontiguousarray(e, np.float64).copy()
+        n = e.shape[0]
+        ld = rho.shape[1]
+        acc = np.ascontiguousarray(accepted, np.uint32)
+        words = acc.shape[1]
+        na = np.ascontiguousarray(n_attempts, np.int32)
+        T_out = np.zeros(n)
+        status = np.zeros(n, np.int32)
+        iters = np.zeros(n, np.int32)
+        T_in = None if T_in is None else np.ascontiguousarray(T_in, np.float64)
+
+        def run(a, b):
+            off8, off4 = a * 8, a * 4
+            lib().om_advance_batch_replay(self.ref, C.byref(o), b - a, ld,
+                                          rho.ctypes.data + off8, e.ctypes.data + off8, float(dt),
+                                          None if T_in is None else T_in.ctypes.data + off8,
+                                          acc.ctypes.data + a * words * 4, words,
+                                          na.ctypes.data + off4, T_out.ctypes.data + off8,
+                                          status.ctypes.data + off4, iters.ctypes.data + off4)
+
+        if threads <= 1 or n < 2 * threads:
+            run(0, n)
+        else:
+            chunk = max(1, (n + 4 * threads - 1) // (4 * threads))
+            with ThreadPoolExecutor(threads) as ex:
+                list(ex.map(lambda a: run(a, min(n, a + chunk)), range(0, n, chunk)))
+        return rho, e, dict(T=T_out, status=status, newton_iters=iters)
+
+    def advance_batch(self, rho, e, dt, T_in=None, opts=None, threads=1, schedule=False, words=8):
         """rho [ns, n] and e [n] float64 (copied); returns new arrays and the
-        per-cell outputs.  threads > 1 splits the cells over host threads."""
+        per-cell outputs.  threads > 1 splits the cells over host threads.
+        schedule=True adds each cell's accepted-attempt bits ([n, words]
+        uint32) to the outputs."""
         o = opts if opts is not None else default_opts()
         rho = np.ascontiguousarray(rho, np.float64).copy()
         e = np.ascontiguousarray(e, np.float64).copy()
@@ -207,17 +275,20 @@ class OracleMech:
         iters = np.zeros(n, np.int32)
         subs = np.zeros(n, np.int32)
         fails = np.zeros(n, np.int32)
+        sched = np.zeros((n, words), np.uint32) if schedule else None
         T_in = None if T_in is None else np.ascontiguousarray(T_in, np.float64)
 
         def run(a, b):
             off8 = a * 8
             off4 = a * 4
-            lib().om_advance_batch(self.ref, C.byref(o), b - a, ld,
-                                   rho.ctypes.data + off8, e.ctypes.data + off8, float(dt),
-                                   None if T_in is None else T_in.ctypes.data + off8,
-                                   T_out.ctypes.data + off8, status.ctypes.data + off4,
-                                   iters.ctypes.data + off4, subs.ctypes.data + off4,
-                                   fails.ctypes.data + off4)
+            lib().om_advance_batch_sched(self.ref, C.byref(o), b - a, ld,
+                                         rho.ctypes.data + off8, e.ctypes.data + off8, float(dt),
+                                         None if T_in is None else T_in.ctypes.data + off8,
+                                         T_out.ctypes.data + off8, status.ctypes.data + off4,
+                                         iters.ctypes.data + off4, subs.ctypes.data + off4,
+                                         fails.ctypes.data + off4,
+                                         None if sched is None else sched.ctypes.data + a * words * 4,
+                                         words if schedule else 0)
 
         if threads <= 1 or n < 2 * threads:
             run(0, n)
@@ -225,8 +296,10 @@ class OracleMech:
             chunk = max(1, (n + 4 * threads - 1) // (4 * threads))
             with ThreadPoolExecutor(threads) as ex:
                 list(ex.map(lambda a: run(a, min(n, a + chunk)), range(0, n, chunk)))
-        return rho, e, dict(T=T_out, status=status, newton_iters=iters, substeps=subs,
-                            failures=fails)
+        out = dict(T=T_out, status=status, newton_iters=iters, substeps=subs, failures=fails)
+        if schedule:
+            out["schedule"] = sched
+        return rho, e, out
 
     def state_from_tpy(self, T, P, Y):
         T = np.ascontiguousarray(T, np.float64)
@@ -243,6 +316,16 @@ class OracleMech:
 def default_opts(**kw) -> Opts:
     o = Opts()
     lib().om_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def replay_opts(**kw) -> Opts:
+    """Options of a replay: every accepted attempt's backward-Euler system is
+    solved to the norm test alone (no contraction-rate stop, no divergence
+    check) with up to 50 Newton iterations."""
+    o = default_opts(conv_kappa=0.0, div_check=0, max_newton=50)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

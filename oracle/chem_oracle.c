@@ -540,9 +540,13 @@ void om_default_opts(om_opts *o)
  * substep is shortened to land exactly on dt.  Time is counted in integer
  * units of dt 2^-max_halvings so the schedule is exact.  On failure the cell
  * keeps its input values.
+ *
+ * With sched != NULL the outcome of every substep attempt is recorded: bit a
+ * (word a / 32, bit a % 32) of sched[0 .. sched_words) is set when attempt a
+ * was accepted; attempts beyond 32 sched_words are not recorded.
  * ------------------------------------------------------------------------- */
-void om_advance_cell(const om_mech *m, const om_opts *o, double *rho, double *e,
-                     double dt, double T_guess, om_cell_result *res)
+static void advance_cell(const om_mech *m, const om_opts *o, double *rho, double *e, double dt,
+                         double T_guess, uint32_t *sched, int sched_words, om_cell_result *res)
 {
     int ns = m->ns, n = ns + 1;
     int s, ti, level = 0, attempts = 0;
@@ -557,6 +561,8 @@ void om_advance_cell(const om_mech *m, const om_opts *o, double *rho, double *e,
     res->substeps = 0;
     res->failures = 0;
     res->T = NAN;
+    for (s = 0; s < sched_words; ++s)
+        sched[s] = 0u;
 
     for (s = 0; s < ns; ++s) {
         x0[s] = rho[s];
@@ -600,6 +606,8 @@ void om_advance_cell(const om_mech *m, const om_opts *o, double *rho, double *e,
         h = ldexp(dt, -level);
         attempts++;
         if (be_substep(m, o, x0, T0, h, atol, x, &T1, &res->newton_iters)) {
+            if (sched && attempts - 1 < 32 * sched_words)
+                sched[(attempts - 1) / 32] |= 1u << ((attempts - 1) % 32);
             memcpy(x0, x, sizeof(double) * (size_t)n);
             T0 = T1;
             t += total >> level;
@@ -625,10 +633,151 @@ out:
     free(atol);
 }
 
+void om_advance_cell(const om_mech *m, const om_opts *o, double *rho, double *e,
+                     double dt, double T_guess, om_cell_result *res)
+{
+    advance_cell(m, o, rho, e, dt, T_guess, NULL, 0, res);
+}
+
+void om_advance_cell_sched(const om_mech *m, const om_opts *o, double *rho, double *e, double dt,
+                           double T_guess, uint32_t *sched, int sched_words, om_cell_result *res)
+{
+    advance_cell(m, o, rho, e, dt, T_guess, sched, sched_words, res);
+}
+
+/* ---------------------------------------------------------------------------
+ * Replay: one cell over dt along a GIVEN substep schedule instead of the one
+ * the control above would choose.  Backward Euler has one solution per
+ * sequence of substep sizes; two integrators whose accept/reject decisions
+ * differ (e.g. because one solves the Newton systems of Eq. 29 in lower
+ * precision) land on different, equally valid discretisations.  This
+ * integrates the schedule the other integrator took, so that its result can
+ * be compared element by element.
+ *
+ * Attempt a (0 <= a < n_attempts) is accepted when bit a of `accepted` is
+ * set.  The sizes follow the same rule as om_advance_cell: h = dt 2^-level,
+ * level raised until the substep fits in the time left, +1 after a rejected
+ * attempt, -1 after an accepted one.  An accepted attempt solves its
+ * backward-Euler system from the current state to the norm test with up to
+ * o->max_newton iterations (the caller's conv_kappa and div_check apply; a
+ * replay normally passes 0 for both), then requires a recoverable T and no
+ * density below -atol, as om_advance_cell does.  A rejected attempt changes
+ * nothing but the level.
+ *
+ * res->status is OM_OK, OM_BAD_INPUT / OM_T_FAILED for the input state,
+ * OM_REPLAY_NOT_CONVERGED when an accepted attempt's system does not
+ * converge, or OM_REPLAY_MISMATCH when the schedule is inconsistent (a level
+ * beyond max_halvings, an attempt after dt is reached, or dt not reached
+ * after n_attempts).  On any status but OM_OK the cell keeps its input.
+ * ------------------------------------------------------------------------- */
+void om_advance_cell_replay(const om_mech *m, const om_opts *o, double *rho, double *e, double dt,
+                            double T_guess, const uint32_t *accepted, int n_attempts,
+                            om_cell_result *res)
+{
+    int ns = m->ns, n = ns + 1;
+    int s, a, ti, level = 0;
+    int64_t total, t = 0;
+    double rho_tot = 0.0, e_scale, T0;
+    double *x0 = (double *)malloc(sizeof(double) * (size_t)n);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *atol = (double *)malloc(sizeof(double) * (size_t)n);
+
+    res->status = OM_OK;
+    res->newton_iters = 0;
+    res->substeps = 0;
+    res->failures = 0;
+    res->T = NAN;
+
+    for (s = 0; s < ns; ++s) {
+        x0[s] = rho[s];
+        rho_tot += rho[s];
+    }
+    x0[ns] = *e;
+    for (s = 0; s < n; ++s) {
+        if (!isfinite(x0[s])) {
+            res->status = OM_BAD_INPUT;
+            goto out;
+        }
+    }
+    if (!(rho_tot > 0.0) || !(dt >= 0.0) || !isfinite(dt)) {
+        res->status = OM_BAD_INPUT;
+        goto out;
+    }
+    if (om_recover_T(m, x0, x0[ns], T_guess, &T0, &ti) != 0) {
+        res->status = OM_T_FAILED;
+        goto out;
+    }
+    res->T = T0;
+    if (dt == 0.0) {
+        if (n_attempts != 0)
+            res->status = OM_REPLAY_MISMATCH;
+        goto out;
+    }
+
+    e_scale = fabs(x0[ns]);
+    for (s = 0; s < ns; ++s) {
+        atol[s] = o->atol_rel * rho_tot;
+        e_scale += fabs(x0[s] * om_species_ef(m, s));
+    }
+    atol[ns] = o->atol_rel * e_scale;
+
+    total = (int64_t)1 << o->max_halvings;
+    for (a = 0; a < n_attempts; ++a) {
+        double h, T1;
+        if (t >= total) {
+            res->status = OM_REPLAY_MISMATCH;
+            goto out;
+        }
+        while ((total >> level) > total - t)
+            level++;
+        h = ldexp(dt, -level);
+        if ((accepted[a / 32] >> (a % 32)) & 1u) {
+            if (!be_substep(m, o, x0, T0, h, atol, x, &T1, &res->newton_iters)) {
+                res->status = OM_REPLAY_NOT_CONVERGED;
+                goto out;
+            }
+            memcpy(x0, x, sizeof(double) * (size_t)n);
+            T0 = T1;
+            t += total >> level;
+            res->substeps++;
+            if (level > 0)
+                level--;
+        } else {
+            res->failures++;
+            level++;
+            if (level > o->max_halvings) {
+                res->status = OM_REPLAY_MISMATCH;
+                goto out;
+            }
+        }
+    }
+    if (t != total) {
+        res->status = OM_REPLAY_MISMATCH;
+        goto out;
+    }
+    for (s = 0; s < ns; ++s)
+        rho[s] = x0[s];
+    *e = x0[ns];
+    res->T = T0;
+out:
+    free(x0);
+    free(x);
+    free(atol);
+}
+
 void om_advance_batch(const om_mech *m, const om_opts *o, long n_cells, long ld,
                       double *rho, double *e, double dt, const double *T_in,
                       double *T_out, int *status, int *newton_iters, int *substeps,
                       int *failures)
+{
+    om_advance_batch_sched(m, o, n_cells, ld, rho, e, dt, T_in, T_out, status, newton_iters,
+                           substeps, failures, NULL, 0);
+}
+
+void om_advance_batch_sched(const om_mech *m, const om_opts *o, long n_cells, long ld,
+                            double *rho, double *e, double dt, const double *T_in,
+                            double *T_out, int *status, int *newton_iters, int *substeps,
+                            int *failures, uint32_t *sched, int sched_words)
 {
     int ns = m->ns;
     long i;
@@ -639,7 +788,8 @@ void om_advance_batch(const om_mech *m, const om_opts *o, long n_cells, long ld,
         double ei = e[i];
         for (s = 0; s < ns; ++s)
             r[s] = rho[(size_t)s * ld + i];
-        om_advance_cell(m, o, r, &ei, dt, T_in ? T_in[i] : 1500.0, &res);
+        advance_cell(m, o, r, &ei, dt, T_in ? T_in[i] : 1500.0,
+                     sched ? sched + (size_t)i * sched_words : NULL, sched ? sched_words : 0, &res);
         for (s = 0; s < ns; ++s)
             rho[(size_t)s * ld + i] = r[s];
         e[i] = ei;
@@ -653,6 +803,44 @@ void om_advance_batch(const om_mech *m, const om_opts *o, long n_cells, long ld,
             substeps[i] = res.substeps;
         if (failures)
             failures[i] = res.failures;
+    }
+    free(r);
+}
+
+/* om_advance_cell_replay over an SoA batch: the schedule of cell i is
+ * accepted[i*sched_words .. (i+1)*sched_words) with n_attempts[i] attempts
+ * (n_attempts[i] <= 32 sched_words). */
+void om_advance_batch_replay(const om_mech *m, const om_opts *o, long n_cells, long ld,
+                             double *rho, double *e, double dt, const double *T_in,
+                             const uint32_t *accepted, int sched_words, const int *n_attempts,
+                             double *T_out, int *status, int *newton_iters)
+{
+    int ns = m->ns;
+    long i;
+    int s;
+    double *r = (double *)malloc(sizeof(double) * (size_t)ns);
+    for (i = 0; i < n_cells; ++i) {
+        om_cell_result res;
+        double ei = e[i];
+        for (s = 0; s < ns; ++s)
+            r[s] = rho[(size_t)s * ld + i];
+        if (n_attempts[i] < 0 || n_attempts[i] > 32 * sched_words) {
+            res.status = OM_REPLAY_MISMATCH;
+            res.newton_iters = 0;
+            res.T = NAN;
+        } else {
+            om_advance_cell_replay(m, o, r, &ei, dt, T_in ? T_in[i] : 1500.0,
+                                   accepted + (size_t)i * sched_words, n_attempts[i], &res);
+        }
+        for (s = 0; s < ns; ++s)
+            rho[(size_t)s * ld + i] = r[s];
+        e[i] = ei;
+        if (T_out)
+            T_out[i] = res.T;
+        if (status)
+            status[i] = res.status;
+        if (newton_iters)
+            newton_iters[i] = res.newton_iters;
     }
     free(r);
 }

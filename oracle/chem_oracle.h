@@ -17,6 +17,8 @@
 #ifndef CHEM_ORACLE_H
 #define CHEM_ORACLE_H
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -61,7 +63,9 @@ enum {
     OM_NEWTON_FAILED = 1,     /* substep halving limit reached                  */
     OM_T_FAILED = 2,          /* temperature of the input state not recoverable */
     OM_BAD_INPUT = 3,         /* non-finite input or non-positive total density */
-    OM_TOO_MANY_STEPS = 4     /* substep attempt budget spent                   */
+    OM_TOO_MANY_STEPS = 4,    /* substep attempt budget spent                   */
+    OM_REPLAY_NOT_CONVERGED = 5, /* replay: an accepted attempt did not converge */
+    OM_REPLAY_MISMATCH = 6    /* replay: the schedule does not add up to dt     */
 };
 
 /* Physical constants of the oracle. */
@@ -108,12 +112,41 @@ void om_advance_cell(const om_mech *m, const om_opts *o,
                      double *rho, double *e, double dt, double T_guess,
                      om_cell_result *res);
 
+/* om_advance_cell that also records which substep attempts were accepted:
+ * bit a of sched[0 .. sched_words) (word a / 32, bit a % 32) is set when
+ * attempt a was accepted. */
+void om_advance_cell_sched(const om_mech *m, const om_opts *o, double *rho, double *e,
+                           double dt, double T_guess, uint32_t *sched, int sched_words,
+                           om_cell_result *res);
+
+/* One cell along a given schedule of accepted / rejected substep attempts
+ * (bit a of `accepted` set: attempt a accepted), each accepted attempt's
+ * backward-Euler system solved to the norm test.  Status OM_OK, OM_BAD_INPUT,
+ * OM_T_FAILED, OM_REPLAY_NOT_CONVERGED or OM_REPLAY_MISMATCH. */
+void om_advance_cell_replay(const om_mech *m, const om_opts *o, double *rho, double *e,
+                            double dt, double T_guess, const uint32_t *accepted, int n_attempts,
+                            om_cell_result *res);
+
+/* The replay over an SoA batch; cell i's schedule is
+ * accepted[i*sched_words ..] with n_attempts[i] attempts. */
+void om_advance_batch_replay(const om_mech *m, const om_opts *o, long n_cells, long ld,
+                             double *rho, double *e, double dt, const double *T_in,
+                             const uint32_t *accepted, int sched_words, const int *n_attempts,
+                             double *T_out, int *status, int *newton_iters);
+
 /* SoA batch: rho[s*ld + cell], e[cell]; in place.  T_in may be NULL (guess
  * 1500 K).  Any of the output arrays may be NULL. */
 void om_advance_batch(const om_mech *m, const om_opts *o, long n_cells, long ld,
                       double *rho, double *e, double dt, const double *T_in,
                       double *T_out, int *status, int *newton_iters,
                       int *substeps, int *failures);
+
+/* om_advance_batch that also records each cell's accepted attempts in
+ * sched[i*sched_words ..] (as om_advance_cell_sched); sched may be NULL. */
+void om_advance_batch_sched(const om_mech *m, const om_opts *o, long n_cells, long ld,
+                            double *rho, double *e, double dt, const double *T_in,
+                            double *T_out, int *status, int *newton_iters, int *substeps,
+                            int *failures, uint32_t *sched, int sched_words);
 
 /* Initial states from (T, P, Y) by Dalton's law (Eq. 5) and the energy
  * definition (Eq. 3).  Y is SoA [s*ld + cell]. */

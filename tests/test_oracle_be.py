@@ -154,7 +154,7 @@ def test_detailed_balance_at_long_times(oracle_mod):
                           if mech.prod_sp[rr, j] >= 0])
             fwd, rev = kf[rr] * Pf, kb[rr] * Pb
             if max(fwd, rev) > 1e-200:
-                assert abs(np.log(fwd) - np.log(rev)) <= 1e-6, (rr, fwd, rev)
+                assert abs(np.log(fwd) - np.log(rev)) <= 1e-8, (rr, fwd, rev)
 
 
 @pytest.mark.parametrize("wl", ["h2air-1k", "hc36-256k"])
