@@ -31,34 +31,46 @@ WORKLOAD_DESC = ("synthetic 36 sp / 308 rxn mechanism (4 elements, 40 third-body
                  "independent unimolecular), 2^18 constant-volume cells, T U[900, 2800] K, 1 atm, "
                  "Dirichlet(1) mass fractions, one dt = 1e-6 s backward-Euler chemistry step with "
                  "adaptive substeps")
-EXP_FLOPS = 40          # one FP64 exp occupies the FP64 pipe like ~20 DFMA (measured)
 # DRAM bytes (read + write) of one launch of the step kernel on the default
 # workload (2^18 cells, state and tables cold after the L2 flush), from a
 # single-pass ncu capture of a full-size launch of the current kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum; part of the state written
-# back is still in L2 when the kernel ends).  Other workloads report null.
-MEASURED_TRAFFIC = {"mixed": 79.99e6 + 31.74e6, "fp64": 80.14e6 + 35.78e6}
+# back is still in L2 when the kernel ends).  None until captured for the
+# kernels as they stand; other workloads report null.
+MEASURED_TRAFFIC = {"mixed": None, "fp64": None}
+# FP64-pipe utilisation of the step kernels from ncu (sm__inst_executed_pipe_fp64
+# share of cycles) on the default workload; None until captured for the
+# kernels as they stand.
+MEASURED_FP64_PIPE = {"mixed": None, "fp64": None}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 x max clock
+FP64_PEAK_PROBE_TFLOPS = 1.193                    # DFMA timing probe on this GPU model
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FFMA/clk x 2 x max clock
 
 
 def work_model(mech):
-    """Algorithmic flops of one Newton iteration of one cell (FMA = 2, exp =
-    EXP_FLOPS), from the mechanism's structure, split into the parts the
-    mixed-precision path keeps in FP64 and the parts it moves to FP32: the
-    Jacobian and LU, the heat capacities (they feed only dT/drho, dT/de and
-    the next temperature guess), the temperature recovery's derivative and
-    the convergence-norm ratios.  All of it is FP64 on the FP64 path.
+    """Algorithmic work of one Newton iteration of one cell, exponentials
+    counted apart from the flops (FMA = 2 flop).
 
-    This counts the method as written (two exponentials per reaction for
-    K_f and K_b, Gaussian elimination on the N_s + 1 unknowns of Eq. 29).
+    fp64_path: the per-iteration count of the method as written -- thermo
+    25 N_s, rates 20 R + 2 N_s R_tb, Jacobian 84 R + 12 N_s R_tb + 5 n^2 +
+    2 n N_s, Gaussian elimination on the n = N_s + 1 unknowns of Eq. 29
+    2 n^3/3 + 2 n^2, residual 3 n -- plus 2 R exponentials (K_f and K_e).
+
+    mixed_fp64 / mixed_fp32: the mixed-precision path's split, counted from
+    the mechanism's structure: what it keeps in FP64 (NASA-7 h, s, g and
+    energies, two temperature-recovery iterations' energy sums, rate
+    constants and progress rates, species sources, residual, update and
+    convergence norm) and what it moves to FP32 (heat capacities and the
+    recovery's derivative, the Jacobian's rate factors, D entries and
+    gather, the elimination).
+
     The kernels do less for the same result: K_b comes from per-species
-    exponentials (one exp per reaction plus one per species), and the energy
-    unknown is eliminated through total-energy conservation (N_s unknowns).
-    The roofline fraction is therefore the method's work rate against the
-    FP64-pipe peak; the pipe's own utilisation is in the ncu counters."""
+    exponentials (one exp per reaction plus one per species, `exp_kernel`),
+    and the energy unknown is eliminated through total-energy conservation
+    (N_s unknowns)."""
     ns, nr = mech.ns, mech.nr
     n = ns + 1
+    ntb = int(np.asarray(mech.third_body).astype(bool).sum())
     nu = np.zeros((nr, ns), np.int64)
     for r in range(nr):
         for j in range(3):
@@ -75,9 +87,11 @@ def work_model(mech):
         nD += len(cols)
         j_ent += len(cols) * rows
         sp_ent += rows
+    fp64_path = (25 * ns + (20 * nr + 2 * ns * ntb) + (84 * nr + 12 * ns * ntb + 5 * n * n + 2 * n * ns) +
+                 (2 * n ** 3 // 3 + 2 * n * n) + 3 * n)
     thermo, thermo_cp = 28 * ns, 10 * ns          # h, s, g, e | c_p, rho c_v
     trec_e, trec_cv = 2 * 14 * ns, 2 * 13 * ns    # two recovery iterations: e(T) | c_v(T)
-    rates_src = 30 * nr + 2 * nr * EXP_FLOPS     # rate constants, progress rates
+    rates_src = 30 * nr                          # rate constants, progress rates (exp apart)
     rates_jac = 10 * nr                          # C_M K_f, C_M K_b, dQ/dT
     d_entries = 8 * nD
     gather_src = 2 * sp_ent + 2 * ns
@@ -85,10 +99,10 @@ def work_model(mech):
     jac = 6 * ns * n + 2 * j_ent + 2 * nD + 6 * n
     lu = sum(2 * (n - j - 1) * (n - j) + (n - j - 1) + 1 for j in range(n)) + n * n
     update, update_norm = 6 * n, 3 * n
-    fp64_core = thermo + trec_e + rates_src + gather_src + update
-    fp32_side = thermo_cp + trec_cv + update_norm + rates_jac + d_entries + gather_jac + jac + lu
-    return dict(flops=fp64_core + fp32_side, mixed_fp64=fp64_core, mixed_fp32=fp32_side,
-                exp=2 * nr, nD=nD, j_ent=j_ent, lu=lu)
+    mixed_fp64 = thermo + trec_e + rates_src + gather_src + update + update_norm
+    mixed_fp32 = thermo_cp + trec_cv + rates_jac + d_entries + gather_jac + jac + lu
+    return dict(fp64_path=fp64_path, mixed_fp64=mixed_fp64, mixed_fp32=mixed_fp32,
+                exp_method=2 * nr, exp_kernel=nr + ns, nD=nD, j_ent=j_ent, ntb=ntb)
 
 
 class Clocks:
@@ -100,12 +114,13 @@ class Clocks:
     def __init__(self, index=0):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="chem_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
@@ -121,10 +136,14 @@ class Clocks:
             except Exception:
                 self.p.kill()
             self.f.close()
+        self._rows = self._read()
+        if self.path:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
 
-    def summary(self):
-        if self.p is None:
-            return None
+    def _read(self):
         rows = []
         try:
             for line in open(self.path):
@@ -132,7 +151,13 @@ class Clocks:
                 if len(parts) >= 9:
                     rows.append(parts)
         except Exception:
+            pass
+        return rows
+
+    def summary(self):
+        if self.p is None:
             return None
+        rows = getattr(self, "_rows", [])
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -453,12 +478,9 @@ def main():
         step_ms = barrier_max(world, statistics.mean(tot), device)
         kern_ms = barrier_max(world, statistics.mean(ker), device)
         it = stats["newton_iters"]
-        if name == "fp64":
-            a64 = it * wm["flops"] / (kern_ms * 1e-3) / 1e12
-            a32 = 0.0
-        else:
-            a64 = it * wm["mixed_fp64"] / (kern_ms * 1e-3) / 1e12
-            a32 = it * wm["mixed_fp32"] / (kern_ms * 1e-3) / 1e12
+        ksec = kern_ms * 1e-3
+        flop64 = wm["fp64_path"] if name == "fp64" else wm["mixed_fp64"]
+        a64 = it * flop64 / ksec / 1e12
         bytes_launch = n * (16 * (mech.ns + 1) + 8)
         full_default = args.workload == WORKLOAD and not args.cells
         roof = {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -466,19 +488,26 @@ def main():
                 "traffic": MEASURED_TRAFFIC[name] if full_default else None,
                 "traffic_unit": "bytes per launch (DRAM read + write)",
                 "kernel": "chem::be_kernel<%d,%s>" % (ch.lanes(prec), "double" if name == "fp64" else "float"),
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe, the "
-                               "binding pipe); probe measured 1.193 TFLOP/s",
-                "work_model": "%d FP64 flop per Newton iteration%s (exp counted as %d), %d Newton "
-                              "iterations per launch; algorithmic count of the method (two exp per "
-                              "reaction, elimination on N_s+1 unknowns), the kernel evaluates one "
-                              "exp per reaction plus one per species and eliminates N_s unknowns" % (
-                                  wm["flops"] if name == "fp64" else wm["mixed_fp64"],
-                                  "" if name == "fp64" else " plus %d FP32 flop" % wm["mixed_fp32"],
-                                  EXP_FLOPS, it),
-                "hbm_gbs": bytes_launch / (kern_ms * 1e-3) / 1e9}
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe, the binding "
+                               "pipe; MEASURED_PEAKS.json has no FP64 figure); a DFMA timing probe "
+                               "measured %.3f TFLOP/s" % FP64_PEAK_PROBE_TFLOPS,
+                "work_model": ("%d FP64 flop per Newton iteration, %s, exponentials apart; %d Newton "
+                               "iterations per launch" % (
+                                   flop64, "the method's count (thermo, rates, Jacobian, elimination on "
+                                   "N_s+1 unknowns, residual)" if name == "fp64" else
+                                   "the part the mixed path keeps in FP64", it)),
+                "exp": {"method_per_iter": wm["exp_method"], "kernel_per_iter": wm["exp_kernel"],
+                        "method_rate_G_per_s": it * wm["exp_method"] / ksec / 1e9,
+                        "evaluated_rate_G_per_s": it * wm["exp_kernel"] / ksec / 1e9},
+                "ncu_fp64_pipe_busy": MEASURED_FP64_PIPE[name] if full_default else None,
+                "hbm_gbs": bytes_launch / ksec / 1e9}
         if name == "mixed":
-            roof["fp32_achieved"] = a32
-            roof["fp32_peak"] = FP32_PEAK_TFLOPS
+            a32 = it * wm["mixed_fp32"] / ksec / 1e12
+            roof["fp32"] = {"achieved": a32, "peak": FP32_PEAK_TFLOPS, "frac": a32 / FP32_PEAK_TFLOPS,
+                            "unit": "TFLOP/s",
+                            "work_model": "%d FP32 flop per Newton iteration (Jacobian, elimination, "
+                                          "heat capacities)" % wm["mixed_fp32"],
+                            "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"}
         results[name] = dict(value=world * n / (step_ms * 1e-3), ms_per_step=step_ms,
                              kernel_ms_per_step=kern_ms, lanes_per_cell=ch.lanes(prec),
                              newton_iters_mean=stats["newton_iters_mean"],

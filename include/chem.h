@@ -146,7 +146,27 @@ typedef struct chem_advance_args {
     void    *stream;          /* cudaStream_t                                  */
     int32_t  precision;       /* -1 = the handle's; else CHEM_FP64 / CHEM_MIXED */
     int32_t  lanes_per_cell;  /* 0 = the handle's choice                        */
+    uint32_t *schedule;       /* diagnostics, device [n_cells*CHEM_SCHEDULE_WORDS], or NULL:
+                                 cell c's substep attempts, bit a (word a/32, bit a%32 of
+                                 schedule[c*CHEM_SCHEDULE_WORDS ..]) set when attempt a was
+                                 accepted.  While recording, the attempt budget is at most
+                                 32*CHEM_SCHEDULE_WORDS (cells beyond it end with
+                                 CHEM_CELL_TOO_MANY_STEPS).  With the counts in substeps and
+                                 failures it fixes the sequence of substep sizes the cell
+                                 took, so a reference integrator can follow the same one. */
+    double  *substep_states;  /* diagnostics, device [n_cells*CHEM_SUBSTEP_STATES*(N_s+1)], or
+                                 NULL: the state (rho_1..rho_Ns, e) after each of cell c's first
+                                 CHEM_SUBSTEP_STATES accepted substeps, at
+                                 [(c*CHEM_SUBSTEP_STATES + j)*(N_s+1) ..]; rows past the cell's
+                                 accepted substeps are left untouched.  Where a substep's
+                                 backward-Euler system has several roots, it tells a reference
+                                 integrator which one the cell took. */
 } chem_advance_args;
+
+/* Words of the per-cell substep-schedule record (256 attempts). */
+#define CHEM_SCHEDULE_WORDS 8
+/* Accepted substeps whose states chem_advance_args.substep_states records. */
+#define CHEM_SUBSTEP_STATES 32
 
 /* chem_advance with strides, temperature guesses and per-cell outputs. */
 int chem_advance_ex(chem_handle_t h, const chem_advance_args *a);

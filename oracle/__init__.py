@@ -94,11 +94,11 @@ def lib():
             L.om_advance_cell.argtypes = [p, p, p, p, d, d, p]
             L.om_advance_batch.argtypes = [p, p, C.c_long, C.c_long, p, p, d, p, p, p, p, p, p]
             L.om_advance_batch_sched.argtypes = [p, p, C.c_long, C.c_long, p, p, d, p, p, p, p, p,
-                                                 p, p, i]
-            L.om_advance_cell_sched.argtypes = [p, p, p, p, d, d, p, i, p]
-            L.om_advance_cell_replay.argtypes = [p, p, p, p, d, d, p, i, p]
+                                                 p, p, i, p, i]
+            L.om_advance_cell_sched.argtypes = [p, p, p, p, d, d, p, i, p, i, p]
+            L.om_advance_cell_replay.argtypes = [p, p, p, p, d, d, p, i, p, i, p]
             L.om_advance_batch_replay.argtypes = [p, p, C.c_long, C.c_long, p, p, d, p, p, i, p,
-                                                  p, p, p]
+                                                  p, i, p, p, p]
             L.om_state_from_tpy.argtypes = [p, C.c_long, C.c_long, p, p, p, p, p]
             _lib = L
     return _lib
@@ -210,26 +210,32 @@ class OracleMech:
         sched = np.zeros(words, np.uint32)
         res = _CellResult()
         lib().om_advance_cell_sched(self.ref, C.byref(o), _ptr(r), C.byref(ev), float(dt),
-                                    float(T_guess), _ptr(sched), words, C.byref(res))
+                                    float(T_guess), _ptr(sched), words, None, 0, C.byref(res))
         return r, ev.value, sched, dict(status=res.status, newton_iters=res.newton_iters,
                                         substeps=res.substeps, failures=res.failures, T=res.T)
 
-    def advance_cell_replay(self, rho, e, dt, accepted, n_attempts, T_guess=1500.0, opts=None):
-        """One cell along the given schedule (om_advance_cell_replay)."""
+    def advance_cell_replay(self, rho, e, dt, accepted, n_attempts, T_guess=1500.0, opts=None,
+                            guides=None):
+        """One cell along the given schedule (om_advance_cell_replay);
+        guides: optional [k, ns+1] states after the other integrator's
+        accepted substeps, Newton's starting points."""
         o = opts if opts is not None else replay_opts()
         r = np.ascontiguousarray(rho, np.float64).copy()
         ev = C.c_double(float(e))
         acc = np.ascontiguousarray(accepted, np.uint32)
+        g = None if guides is None else np.ascontiguousarray(guides, np.float64)
         res = _CellResult()
         lib().om_advance_cell_replay(self.ref, C.byref(o), _ptr(r), C.byref(ev), float(dt),
-                                     float(T_guess), _ptr(acc), int(n_attempts), C.byref(res))
+                                     float(T_guess), _ptr(acc), int(n_attempts), _ptr(g),
+                                     0 if g is None else g.shape[0], C.byref(res))
         return r, ev.value, dict(status=res.status, newton_iters=res.newton_iters,
                                  substeps=res.substeps, failures=res.failures, T=res.T)
 
     def advance_batch_replay(self, rho, e, dt, accepted, n_attempts, T_in=None, opts=None,
-                             threads=1):
-        """The replay over a batch: accepted [n, words] uint32, n_attempts [n].
-        Returns new rho, e and dict(T, status, newton_iters)."""
+                             threads=1, guides=None):
+        """The replay over a batch: accepted [n, words] uint32, n_attempts [n],
+        guides optional [n, k, ns+1].  Returns new rho, e and dict(T, status,
+        newton_iters)."""
         o = opts if opts is not None else replay_opts()
         rho = np.ascontiguousarray(rho, np.float64).copy()
         e = np.ascontiguousarray(e, np.float64).copy()
@@ -238,6 +244,8 @@ class OracleMech:
         acc = np.ascontiguousarray(accepted, np.uint32)
         words = acc.shape[1]
         na = np.ascontiguousarray(n_attempts, np.int32)
+        g = None if guides is None else np.ascontiguousarray(guides, np.float64)
+        ng = 0 if g is None else g.shape[1]
         T_out = np.zeros(n)
         status = np.zeros(n, np.int32)
         iters = np.zeros(n, np.int32)
@@ -249,7 +257,9 @@ class OracleMech:
                                           rho.ctypes.data + off8, e.ctypes.data + off8, float(dt),
                                           None if T_in is None else T_in.ctypes.data + off8,
                                           acc.ctypes.data + a * words * 4, words,
-                                          na.ctypes.data + off4, T_out.ctypes.data + off8,
+                                          na.ctypes.data + off4,
+                                          None if g is None else g.ctypes.data + a * ng * self.n * 8,
+                                          ng, T_out.ctypes.data + off8,
                                           status.ctypes.data + off4, iters.ctypes.data + off4)
 
         if threads <= 1 or n < 2 * threads:
@@ -260,11 +270,13 @@ class OracleMech:
                 list(ex.map(lambda a: run(a, min(n, a + chunk)), range(0, n, chunk)))
         return rho, e, dict(T=T_out, status=status, newton_iters=iters)
 
-    def advance_batch(self, rho, e, dt, T_in=None, opts=None, threads=1, schedule=False, words=8):
+    def advance_batch(self, rho, e, dt, T_in=None, opts=None, threads=1, schedule=False, words=8,
+                      states_cap=0):
         """rho [ns, n] and e [n] float64 (copied); returns new arrays and the
         per-cell outputs.  threads > 1 splits the cells over host threads.
         schedule=True adds each cell's accepted-attempt bits ([n, words]
-        uint32) to the outputs."""
+        uint32) to the outputs; states_cap > 0 adds its states after the
+        first states_cap accepted substeps ([n, states_cap, ns+1])."""
         o = opts if opts is not None else default_opts()
         rho = np.ascontiguousarray(rho, np.float64).copy()
         e = np.ascontiguousarray(e, np.float64).copy()
@@ -276,6 +288,7 @@ class OracleMech:
         subs = np.zeros(n, np.int32)
         fails = np.zeros(n, np.int32)
         sched = np.zeros((n, words), np.uint32) if schedule else None
+        states = np.zeros((n, states_cap, self.n)) if states_cap > 0 else None
         T_in = None if T_in is None else np.ascontiguousarray(T_in, np.float64)
 
         def run(a, b):
@@ -288,7 +301,10 @@ class OracleMech:
                                          iters.ctypes.data + off4, subs.ctypes.data + off4,
                                          fails.ctypes.data + off4,
                                          None if sched is None else sched.ctypes.data + a * words * 4,
-                                         words if schedule else 0)
+                                         words if schedule else 0,
+                                         None if states is None else
+                                         states.ctypes.data + a * states_cap * self.n * 8,
+                                         states_cap)
 
         if threads <= 1 or n < 2 * threads:
             run(0, n)
@@ -299,6 +315,8 @@ class OracleMech:
         out = dict(T=T_out, status=status, newton_iters=iters, substeps=subs, failures=fails)
         if schedule:
             out["schedule"] = sched
+        if states is not None:
+            out["states"] = states
         return rho, e, out
 
     def state_from_tpy(self, T, P, Y):

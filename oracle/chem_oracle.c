@@ -445,8 +445,8 @@ void om_lu_solve(int n, const double *LU, const int *piv, double *b)
  * temperature is recoverable and no density is below -atol.
  * ------------------------------------------------------------------------- */
 static int be_substep(const om_mech *m, const om_opts *o, const double *x0, double T0,
-                      double h, const double *atol, double *x, double *T_out,
-                      int *iters)
+                      double h, const double *atol, const double *xstart, double *x,
+                      double *T_out, int *iters)
 {
     int ns = m->ns, n = ns + 1;
     int i, k, ti, ok = 0;
@@ -456,11 +456,13 @@ static int be_substep(const om_mech *m, const om_opts *o, const double *x0, doub
     double *b = (double *)malloc(sizeof(double) * (size_t)n);
     int *piv = (int *)malloc(sizeof(int) * (size_t)n);
 
-    memcpy(x, x0, sizeof(double) * (size_t)n);
+    /* Newton starts from x0 (T0 = T(x0) for the first iteration), or from a
+     * given state xstart (its temperature recovered first) */
+    memcpy(x, xstart ? xstart : x0, sizeof(double) * (size_t)n);
     for (k = 0; k < o->max_newton; ++k) {
         double norm = 0.0;
         int finite = 1;
-        if (k > 0 && om_recover_T(m, x, x[ns], T, &T, &ti) != 0)
+        if ((k > 0 || xstart) && om_recover_T(m, x, x[ns], T, &T, &ti) != 0)
             goto done;
         *iters += 1;
         om_source(m, x, T, w);
@@ -543,10 +545,13 @@ void om_default_opts(om_opts *o)
  *
  * With sched != NULL the outcome of every substep attempt is recorded: bit a
  * (word a / 32, bit a % 32) of sched[0 .. sched_words) is set when attempt a
- * was accepted; attempts beyond 32 sched_words are not recorded.
+ * was accepted; attempts beyond 32 sched_words are not recorded.  With
+ * states != NULL the state after accepted substep j < states_cap is copied to
+ * states[j*(N_s+1) ..].
  * ------------------------------------------------------------------------- */
 static void advance_cell(const om_mech *m, const om_opts *o, double *rho, double *e, double dt,
-                         double T_guess, uint32_t *sched, int sched_words, om_cell_result *res)
+                         double T_guess, uint32_t *sched, int sched_words, double *states,
+                         int states_cap, om_cell_result *res)
 {
     int ns = m->ns, n = ns + 1;
     int s, ti, level = 0, attempts = 0;
@@ -605,9 +610,11 @@ static void advance_cell(const om_mech *m, const om_opts *o, double *rho, double
             level++;
         h = ldexp(dt, -level);
         attempts++;
-        if (be_substep(m, o, x0, T0, h, atol, x, &T1, &res->newton_iters)) {
+        if (be_substep(m, o, x0, T0, h, atol, NULL, x, &T1, &res->newton_iters)) {
             if (sched && attempts - 1 < 32 * sched_words)
                 sched[(attempts - 1) / 32] |= 1u << ((attempts - 1) % 32);
+            if (states && res->substeps < states_cap)
+                memcpy(states + (size_t)res->substeps * n, x, sizeof(double) * (size_t)n);
             memcpy(x0, x, sizeof(double) * (size_t)n);
             T0 = T1;
             t += total >> level;
@@ -636,13 +643,14 @@ out:
 void om_advance_cell(const om_mech *m, const om_opts *o, double *rho, double *e,
                      double dt, double T_guess, om_cell_result *res)
 {
-    advance_cell(m, o, rho, e, dt, T_guess, NULL, 0, res);
+    advance_cell(m, o, rho, e, dt, T_guess, NULL, 0, NULL, 0, res);
 }
 
 void om_advance_cell_sched(const om_mech *m, const om_opts *o, double *rho, double *e, double dt,
-                           double T_guess, uint32_t *sched, int sched_words, om_cell_result *res)
+                           double T_guess, uint32_t *sched, int sched_words, double *states,
+                           int states_cap, om_cell_result *res)
 {
-    advance_cell(m, o, rho, e, dt, T_guess, sched, sched_words, res);
+    advance_cell(m, o, rho, e, dt, T_guess, sched, sched_words, states, states_cap, res);
 }
 
 /* ---------------------------------------------------------------------------
@@ -664,6 +672,15 @@ void om_advance_cell_sched(const om_mech *m, const om_opts *o, double *rho, doub
  * density below -atol, as om_advance_cell does.  A rejected attempt changes
  * nothing but the level.
  *
+ * Where a substep's backward-Euler system has several roots, Newton's method
+ * started from the current state may reach another root than the other
+ * integrator did, or none (hot cells at large h, where the iteration's global
+ * phase is chaotic).  `guides` (optional, n_guides states of N_s + 1 values)
+ * carries the other integrator's state after each of its accepted substeps;
+ * accepted substep j then starts Newton from guides[j] instead of the current
+ * state.  The root is still the oracle's own, of the system set up from the
+ * oracle's own previous state; the guide only selects which root.
+ *
  * res->status is OM_OK, OM_BAD_INPUT / OM_T_FAILED for the input state,
  * OM_REPLAY_NOT_CONVERGED when an accepted attempt's system does not
  * converge, or OM_REPLAY_MISMATCH when the schedule is inconsistent (a level
@@ -672,7 +689,7 @@ void om_advance_cell_sched(const om_mech *m, const om_opts *o, double *rho, doub
  * ------------------------------------------------------------------------- */
 void om_advance_cell_replay(const om_mech *m, const om_opts *o, double *rho, double *e, double dt,
                             double T_guess, const uint32_t *accepted, int n_attempts,
-                            om_cell_result *res)
+                            const double *guides, int n_guides, om_cell_result *res)
 {
     int ns = m->ns, n = ns + 1;
     int s, a, ti, level = 0;
@@ -732,7 +749,9 @@ void om_advance_cell_replay(const om_mech *m, const om_opts *o, double *rho, dou
             level++;
         h = ldexp(dt, -level);
         if ((accepted[a / 32] >> (a % 32)) & 1u) {
-            if (!be_substep(m, o, x0, T0, h, atol, x, &T1, &res->newton_iters)) {
+            const double *g =
+                guides && res->substeps < n_guides ? guides + (size_t)res->substeps * n : NULL;
+            if (!be_substep(m, o, x0, T0, h, atol, g, x, &T1, &res->newton_iters)) {
                 res->status = OM_REPLAY_NOT_CONVERGED;
                 goto out;
             }
@@ -771,13 +790,14 @@ void om_advance_batch(const om_mech *m, const om_opts *o, long n_cells, long ld,
                       int *failures)
 {
     om_advance_batch_sched(m, o, n_cells, ld, rho, e, dt, T_in, T_out, status, newton_iters,
-                           substeps, failures, NULL, 0);
+                           substeps, failures, NULL, 0, NULL, 0);
 }
 
 void om_advance_batch_sched(const om_mech *m, const om_opts *o, long n_cells, long ld,
                             double *rho, double *e, double dt, const double *T_in,
                             double *T_out, int *status, int *newton_iters, int *substeps,
-                            int *failures, uint32_t *sched, int sched_words)
+                            int *failures, uint32_t *sched, int sched_words, double *states,
+                            int states_cap)
 {
     int ns = m->ns;
     long i;
@@ -789,7 +809,9 @@ void om_advance_batch_sched(const om_mech *m, const om_opts *o, long n_cells, lo
         for (s = 0; s < ns; ++s)
             r[s] = rho[(size_t)s * ld + i];
         advance_cell(m, o, r, &ei, dt, T_in ? T_in[i] : 1500.0,
-                     sched ? sched + (size_t)i * sched_words : NULL, sched ? sched_words : 0, &res);
+                     sched ? sched + (size_t)i * sched_words : NULL, sched ? sched_words : 0,
+                     states ? states + (size_t)i * states_cap * (ns + 1) : NULL,
+                     states ? states_cap : 0, &res);
         for (s = 0; s < ns; ++s)
             rho[(size_t)s * ld + i] = r[s];
         e[i] = ei;
@@ -813,7 +835,8 @@ void om_advance_batch_sched(const om_mech *m, const om_opts *o, long n_cells, lo
 void om_advance_batch_replay(const om_mech *m, const om_opts *o, long n_cells, long ld,
                              double *rho, double *e, double dt, const double *T_in,
                              const uint32_t *accepted, int sched_words, const int *n_attempts,
-                             double *T_out, int *status, int *newton_iters)
+                             const double *guides, int n_guides, double *T_out, int *status,
+                             int *newton_iters)
 {
     int ns = m->ns;
     long i;
@@ -830,7 +853,9 @@ void om_advance_batch_replay(const om_mech *m, const om_opts *o, long n_cells, l
             res.T = NAN;
         } else {
             om_advance_cell_replay(m, o, r, &ei, dt, T_in ? T_in[i] : 1500.0,
-                                   accepted + (size_t)i * sched_words, n_attempts[i], &res);
+                                   accepted + (size_t)i * sched_words, n_attempts[i],
+                                   guides ? guides + (size_t)i * n_guides * (ns + 1) : NULL,
+                                   n_guides, &res);
         }
         for (s = 0; s < ns; ++s)
             rho[(size_t)s * ld + i] = r[s];

@@ -114,25 +114,30 @@ void om_advance_cell(const om_mech *m, const om_opts *o,
 
 /* om_advance_cell that also records which substep attempts were accepted:
  * bit a of sched[0 .. sched_words) (word a / 32, bit a % 32) is set when
- * attempt a was accepted. */
+ * attempt a was accepted; and, with states != NULL, the state after each of
+ * the first states_cap accepted substeps (N_s + 1 values each). */
 void om_advance_cell_sched(const om_mech *m, const om_opts *o, double *rho, double *e,
                            double dt, double T_guess, uint32_t *sched, int sched_words,
-                           om_cell_result *res);
+                           double *states, int states_cap, om_cell_result *res);
 
 /* One cell along a given schedule of accepted / rejected substep attempts
  * (bit a of `accepted` set: attempt a accepted), each accepted attempt's
- * backward-Euler system solved to the norm test.  Status OM_OK, OM_BAD_INPUT,
- * OM_T_FAILED, OM_REPLAY_NOT_CONVERGED or OM_REPLAY_MISMATCH. */
+ * backward-Euler system solved to the norm test; Newton for accepted substep
+ * j starts from guides[j*(N_s+1) ..] when j < n_guides (guides may be NULL),
+ * else from the current state.  Status OM_OK, OM_BAD_INPUT, OM_T_FAILED,
+ * OM_REPLAY_NOT_CONVERGED or OM_REPLAY_MISMATCH. */
 void om_advance_cell_replay(const om_mech *m, const om_opts *o, double *rho, double *e,
                             double dt, double T_guess, const uint32_t *accepted, int n_attempts,
-                            om_cell_result *res);
+                            const double *guides, int n_guides, om_cell_result *res);
 
 /* The replay over an SoA batch; cell i's schedule is
- * accepted[i*sched_words ..] with n_attempts[i] attempts. */
+ * accepted[i*sched_words ..] with n_attempts[i] attempts, its guides (may be
+ * NULL) guides[i*n_guides*(N_s+1) ..]. */
 void om_advance_batch_replay(const om_mech *m, const om_opts *o, long n_cells, long ld,
                              double *rho, double *e, double dt, const double *T_in,
                              const uint32_t *accepted, int sched_words, const int *n_attempts,
-                             double *T_out, int *status, int *newton_iters);
+                             const double *guides, int n_guides, double *T_out, int *status,
+                             int *newton_iters);
 
 /* SoA batch: rho[s*ld + cell], e[cell]; in place.  T_in may be NULL (guess
  * 1500 K).  Any of the output arrays may be NULL. */
@@ -142,11 +147,14 @@ void om_advance_batch(const om_mech *m, const om_opts *o, long n_cells, long ld,
                       int *substeps, int *failures);
 
 /* om_advance_batch that also records each cell's accepted attempts in
- * sched[i*sched_words ..] (as om_advance_cell_sched); sched may be NULL. */
+ * sched[i*sched_words ..] and its states after accepted substeps in
+ * states[i*states_cap*(N_s+1) ..] (as om_advance_cell_sched); sched and
+ * states may be NULL. */
 void om_advance_batch_sched(const om_mech *m, const om_opts *o, long n_cells, long ld,
                             double *rho, double *e, double dt, const double *T_in,
                             double *T_out, int *status, int *newton_iters, int *substeps,
-                            int *failures, uint32_t *sched, int sched_words);
+                            int *failures, uint32_t *sched, int sched_words, double *states,
+                            int states_cap);
 
 /* Initial states from (T, P, Y) by Dalton's law (Eq. 5) and the energy
  * definition (Eq. 3).  Y is SoA [s*ld + cell]. */

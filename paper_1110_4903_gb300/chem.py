@@ -49,7 +49,12 @@ class AdvanceArgs(C.Structure):
                 ("dt", C.c_double), ("T_in", C.c_void_p), ("T_out", C.c_void_p),
                 ("status", C.c_void_p), ("newton_iters", C.c_void_p), ("substeps", C.c_void_p),
                 ("failures", C.c_void_p), ("stream", C.c_void_p), ("precision", C.c_int32),
-                ("lanes_per_cell", C.c_int32)]
+                ("lanes_per_cell", C.c_int32), ("schedule", C.c_void_p),
+                ("substep_states", C.c_void_p)]
+
+
+SCHEDULE_WORDS = 8   # CHEM_SCHEDULE_WORDS
+SUBSTEP_STATES = 32  # CHEM_SUBSTEP_STATES
 
 
 class ServerOptions(C.Structure):
@@ -216,22 +221,29 @@ class Chem:
 
     def advance(self, rho, e, dt, *, n_cells=None, T_in=None, T_out=None, status=None,
                 newton_iters=None, substeps=None, failures=None, precision=-1, lanes=0,
-                stream=None):
-        """In-place step of device tensors rho [ns, ld] and e [>= n] (float64)."""
+                stream=None, schedule=None, substep_states=None):
+        """In-place step of device tensors rho [ns, ld] and e [>= n] (float64).
+        schedule: optional int32 device tensor [n, SCHEDULE_WORDS] that receives
+        each cell's accepted-attempt bits; substep_states: optional float64
+        device tensor [n, SUBSTEP_STATES, ns+1] that receives its states after
+        accepted substeps."""
         n = int(e.shape[0]) if n_cells is None else int(n_cells)
         a = AdvanceArgs(n, int(rho.stride(0)), rho.data_ptr(), e.data_ptr(), float(dt),
                         _ptr(T_in), _ptr(T_out), _ptr(status), _ptr(newton_iters), _ptr(substeps),
-                        _ptr(failures), _stream_ptr(stream), int(precision), int(lanes))
+                        _ptr(failures), _stream_ptr(stream), int(precision), int(lanes),
+                        _ptr(schedule), _ptr(substep_states))
         check(lib().chem_advance_ex(self.h, C.byref(a)))
 
     def advance_segmented(self, rho, e, dt, segment_cells, *, n_cells=None, T_in=None, T_out=None,
-                          status=None, precision=-1, stream=None):
+                          status=None, newton_iters=None, substeps=None, failures=None,
+                          precision=-1, stream=None, schedule=None, substep_states=None):
         """chem_advance_segmented: the same step in launches of at most
         segment_cells cells."""
         n = int(e.shape[0]) if n_cells is None else int(n_cells)
         a = AdvanceArgs(n, int(rho.stride(0)), rho.data_ptr(), e.data_ptr(), float(dt),
-                        _ptr(T_in), _ptr(T_out), _ptr(status), None, None, None,
-                        _stream_ptr(stream), int(precision), 0)
+                        _ptr(T_in), _ptr(T_out), _ptr(status), _ptr(newton_iters), _ptr(substeps),
+                        _ptr(failures), _stream_ptr(stream), int(precision), 0, _ptr(schedule),
+                        _ptr(substep_states))
         check(lib().chem_advance_segmented(self.h, C.byref(a), int(segment_cells)))
 
     def advance_simple(self, n_cells, rho, e, dt, stream=None):

@@ -723,6 +723,9 @@ __global__ void temperature_kernel(DeviceMech m, long long n, long long ld, cons
     Tout[i] = ok ? T : NAN;
 }
 
+static_assert(kSchedWords == CHEM_SCHEDULE_WORDS, "schedule record size");
+static_assert(kSubstepStates == CHEM_SUBSTEP_STATES, "substep-state record size");
+
 int launch_step(Handle *h, const chem_advance_args *a, int prec, int G, unsigned long long *counter) {
     LaunchCfg *cfg = nullptr;
     int rc = get_cfg(h, prec, G, &cfg);
@@ -753,6 +756,9 @@ int launch_cfg(Handle *h, const chem_advance_args *a, int prec, const LaunchCfg 
     b.substeps = a->substeps;
     b.failures = a->failures;
     b.work_counter = counter;
+    b.schedule = a->schedule;
+    b.substep_states = a->substep_states;
+    if (a->schedule) o.max_attempts = std::min(o.max_attempts, 32 * kSchedWords);
     // no more blocks than it takes to give every cell a slot
     const long long slots_per_block = (long long)(cfg->block / 32) * (32 / cfg->G);
     long long grid = std::min<long long>(cfg->grid, (b.n_cells + slots_per_block - 1) / slots_per_block);
@@ -909,6 +915,9 @@ int chem_advance_segmented(chem_handle_t hh, const chem_advance_args *a, int64_t
         s.newton_iters = a->newton_iters ? a->newton_iters + off : nullptr;
         s.substeps = a->substeps ? a->substeps + off : nullptr;
         s.failures = a->failures ? a->failures + off : nullptr;
+        s.schedule = a->schedule ? a->schedule + off * CHEM_SCHEDULE_WORDS : nullptr;
+        s.substep_states =
+            a->substep_states ? a->substep_states + off * CHEM_SUBSTEP_STATES * (h->ns + 1) : nullptr;
         const int rc = chem_advance_ex(h, &s);
         if (rc) return rc;
     }

@@ -154,7 +154,19 @@ struct StepBatch {
     int *substeps;
     int *failures;
     unsigned long long *work_counter;   // zeroed before the launch
+    // optional record of the substep schedule: kSchedWords words per cell,
+    // bit a set when attempt a was accepted (the attempt budget is capped at
+    // 32 kSchedWords while recording)
+    unsigned *schedule;
+    // optional record of the state after each of a cell's first kSubstepStates
+    // accepted substeps: [cell][substep][ns + 1]
+    double *substep_states;
 };
+
+// Words of the per-cell substep-schedule record (256 attempts).
+constexpr int kSchedWords = 8;
+// Accepted substeps whose states a cell records.
+constexpr int kSubstepStates = 32;
 
 // Per-cell status codes (same values as the public CHEM_CELL_*).
 enum CellStatus { kCellOk = 0, kCellNewtonFailed = 1, kCellTFailed = 2, kCellBadInput = 3,

@@ -73,10 +73,24 @@ struct Grp {
         for (int o = G / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
         return v;
     }
-    // maximum of non-negative floats (their bit patterns order the same way)
-    __device__ __forceinline__ static float max_nonneg(float v) {
-        if (G == 32) return __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(v)));
-        return max(v);
+    // maximum of non-negative doubles on the integer pipe (their bit
+    // patterns order the same way; a NaN, whose bits are larger than any
+    // number's, wins): for a whole warp the high words by redux.sync, then
+    // the low words of the lanes holding the high maximum
+    __device__ __forceinline__ static double max_nonneg(double v) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        if (G == 32) {
+            const unsigned hi = (unsigned)(b >> 32);
+            const unsigned mhi = __reduce_max_sync(kFull, hi);
+            const unsigned mlo = __reduce_max_sync(kFull, hi == mhi ? (unsigned)b : 0u);
+            return __longlong_as_double((long long)(((unsigned long long)mhi << 32) | mlo));
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const unsigned long long b2 = __shfl_xor_sync(kFull, b, o);
+            b = b2 > b ? b2 : b;
+        }
+        return __longlong_as_double((long long)b);
     }
     // largest key, lowest index on ties
     __device__ __forceinline__ static void argmax(unsigned long long &k, int &i) {
@@ -910,11 +924,16 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
 
     // 8. update, convergence norm, and the linearised temperature of the
     //    new iterate (dT = (de - sum_s e_s^sens drho_s) / (rho cv)) as the
-    //    next recovery's starting guess
-    //    (the FP32 path takes the norm's ratios in FP32: they decide
-    //    convergence, not the iterate)
+    //    next recovery's starting guess.  The norm's ratios are FP64 on both
+    //    paths (they decide acceptance and the divergence abort) and their
+    //    maximum is taken on the bit patterns; a zero scale counts a nonzero
+    //    update as infinitely large.
+    auto ratio = [](double d, double den) -> double {
+        if (__double_as_longlong(den) > 0) return fabs(d) * frcp1(den);
+        return (__double_as_longlong(d) << 1) != 0 ? CUDART_INF : 0.0;
+    };
     double nrm = 0.0, des = 0.0, se = 0.0;
-    float nrmf = 0.f, desf = 0.f, sef = 0.f;
+    float desf = 0.f, sef = 0.f;
     int nonfinite = 0;
 #pragma unroll 1
     for (int i = sl; i < N; i += G) {
@@ -933,16 +952,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const double xi = sm.x[i] + d;
         sm.x[i] = xi;
         if (!finite_bits(xi)) nonfinite = 1;
-        const double den = fma(rtol, fabs(xi), atol_rho);
-        // a zero scale counts a nonzero update as infinitely large
-        if (f32) {
-            const float denf = d2f_rz(den), adf = fabsf(df);
-            const float ri = denf > 0.f ? adf * __frcp_rn(denf) : (adf != 0.f ? CUDART_INF_F : 0.f);
-            nrmf = fmaxf(nrmf, ri);
-        } else {
-            const double ri = den > 0.0 ? fabs(d) * frcp1(den) : (d != 0.0 ? CUDART_INF : 0.0);
-            nrm = fmax(nrm, ri);
-        }
+        const double ri = ratio(d, fma(rtol, fabs(xi), atol_rho));
+        if (bits_gt(ri, nrm)) nrm = ri;
     }
     {
         // the eliminated energy unknown: de = -R_E - e_f . drho
@@ -951,23 +962,15 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             const double xe = sm.x[ns] + de;
             sm.x[ns] = xe;
             if (!finite_bits(xe)) nonfinite = 1;
-            const double den = fma(rtol, fabs(xe), atol_e);
-            if (f32) {
-                const float denf = d2f_rz(den), adf = fabsf(d2f_rz(de));
-                const float ri = denf > 0.f ? adf * __frcp_rn(denf) : (adf != 0.f ? CUDART_INF_F : 0.f);
-                nrmf = fmaxf(nrmf, ri);
+            const double ri = ratio(de, fma(rtol, fabs(xe), atol_e));
+            if (bits_gt(ri, nrm)) nrm = ri;
+            if (f32)
                 desf += d2f_rz(de);
-            } else {
-                const double ri = den > 0.0 ? fabs(de) * frcp1(den) : (de != 0.0 ? CUDART_INF : 0.0);
-                nrm = fmax(nrm, ri);
+            else
                 des += de;
-            }
         }
     }
-    if (f32)
-        nrm = f2d_alu(Grp<G>::max_nonneg(nrmf));
-    else
-        nrm = Grp<G>::max(nrm);
+    nrm = Grp<G>::max_nonneg(nrm);
     nonfinite = Grp<G>::any(nonfinite);
     if (f32)
         des = f2d_alu(Grp<G>::sum(desf));
@@ -1055,6 +1058,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
                 cell = got;
                 iters = subs = fails = 0;
                 Tin = CUDART_NAN;
+                if (b.schedule && sl == 0) {
+#pragma unroll 1
+                    for (int w = 0; w < kSchedWords; ++w) b.schedule[cell * kSchedWords + w] = 0u;
+                }
 #pragma unroll 1
                 for (int i = sl; i < n; i += G) {
                     const double v = i < ns ? b.rho[(size_t)i * b.ld + cell] : b.e[cell];
@@ -1126,7 +1133,17 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
                     substep_fail();
                 } else {
                     T = Tr;
-                    // accept the substep
+                    // accept the substep (and record it: attempt attempts - 1
+                    // < 32 kSchedWords, the budget being capped when recording)
+                    if (b.schedule && sl == 0) {
+                        const int a = attempts - 1;
+                        b.schedule[cell * kSchedWords + (a >> 5)] |= 1u << (a & 31);
+                    }
+                    if (b.substep_states && subs < kSubstepStates) {
+                        double *rec = b.substep_states + ((size_t)cell * kSubstepStates + subs) * n;
+#pragma unroll 1
+                        for (int i = sl; i < n; i += G) rec[i] = sm.x[i];
+                    }
 #pragma unroll 1
                     for (int i = sl; i < n; i += G) sm.x0[i] = sm.x[i];
                     T0 = T;

@@ -7,9 +7,11 @@ nothing); run it on a GPU machine:
 
 Species use the tests' floor (1e-12 of the cell density) below which
 differences count as absolute.  "same path" are the cells whose substep
-decisions (accepted substeps and failed attempts) equal the oracle's; the
-others took a different, equally valid halving sequence and are reported
-separately.
+schedule (the accepted / rejected sequence of attempts) equals the
+oracle's; every finished cell is also compared with the oracle integrating
+it along the GPU's own schedule (the replay), which covers the cells that
+took a different, equally valid halving sequence.  Uniform and hottest
+cells are reported separately.
 """
 import argparse
 import json
@@ -26,37 +28,49 @@ import parity as P  # noqa: E402
 from paper_1110_4903_gb300 import synth  # noqa: E402
 
 
-def sample(f, n, seed=0):
-    """n cells: half uniformly spread, half the hottest (the stiff ones)."""
+def samples(f, n, seed=0):
+    """n uniformly spread cells, and the n hottest (the stiff ones)."""
     if n >= f.n:
-        return np.arange(f.n)
+        return {"all": np.arange(f.n)}
     rng = np.random.default_rng(seed)
-    hot = np.argsort(f.T)[-4 * n:]
-    idx = np.unique(np.concatenate([rng.choice(f.n, n // 2, replace=False), rng.choice(hot, n - n // 2, replace=False)]))
-    return np.sort(idx)
+    return {"uniform": np.sort(rng.choice(f.n, n, replace=False)),
+            "hottest": np.sort(np.argsort(-f.T, kind="stable")[:n])}
 
 
-def stats(rg, eg, og, rr, er, oo, rho0):
-    ok = oo["status"] == 0
-    same = ok & (og["substeps"] == oo["substeps"]) & (og["failures"] == oo["failures"])
-    rel = P.rel_species(rg, rr, rho0.sum(0))
-    relT = np.abs(og["T"] - oo["T"]) / np.abs(oo["T"])
-    rel_e = np.abs(eg - er) / (np.abs(er) + np.abs(rho0).sum(0) * 1e6)
+def _q(a):
+    a = a.max(0) if a.ndim == 2 else a
+    return (float(a.max()), float(np.percentile(a, 99))) if a.size else (0.0, 0.0)
 
-    def q(a, m):
-        a = a[..., m].ravel() if a.ndim == 2 else a[m]
-        return (float(a.max()), float(np.percentile(a, 99))) if a.size else (0.0, 0.0)
 
+def replay(mech, rho0, e0, dt, T_in, og, threads, **opts):
+    """The oracle along the GPU's own schedule, for the cells it finished."""
+    ok = og["status"] == 0
+    om = P.oracle.OracleMech(mech)
+    na = og["substeps"] + og["failures"]
+    return om.advance_batch_replay(rho0[:, ok], e0[ok], dt, og["schedule"][ok], na[ok], T_in=T_in[ok],
+                                   threads=threads, opts=P.oracle.replay_opts(**opts),
+                                   guides=og["states"][ok])
+
+
+def stats(rho0, rg, eg, og, rr, er, oo, rep, floor):
+    ok = og["status"] == 0
+    same = P.same_path(og, oo)
     out = dict(cells=int(len(ok)), status_equal=bool(np.array_equal(og["status"], oo["status"])),
                same_path=float(same.sum() / max(1, ok.sum())))
-    for name, a in (("species", rel), ("T", relT), ("e", rel_e)):
-        mx, p99 = q(a, same)
-        out[name + "_max"] = mx
-        out[name + "_p99"] = p99
-    flip = ok & ~same
-    if flip.any():
-        out["other_path_species_max"] = float(rel[:, flip].max())
-        out["other_path_T_max"] = float(relT[flip].max())
+    rel = P.rel_species(rg, rr, rho0.sum(0), floor)
+    relT = np.abs(og["T"] - oo["T"]) / np.abs(oo["T"])
+    out["same_path_species_max"], out["same_path_species_p99"] = _q(rel[:, same])
+    out["same_path_T_max"], _ = _q(relT[same])
+    # every finished cell against the replay of its own schedule
+    rp, ep, orp = rep
+    good = orp["status"] == 0
+    out["replay_failed"] = int((~good).sum())
+    relr = P.rel_species(rg[:, ok][:, good], rp[:, good], rho0[:, ok][:, good].sum(0), floor)
+    relTr = np.abs(og["T"][ok][good] - orp["T"][good]) / orp["T"][good]
+    rele = np.abs(eg[ok][good] - ep[good]) / (np.abs(ep[good]) + np.abs(rho0[:, ok][:, good]).sum(0) * 1e6)
+    out["all_cells_species_max"], out["all_cells_species_p99"] = _q(relr)
+    out["all_cells_T_max"], out["all_cells_T_p99"] = _q(relTr)
+    out["all_cells_e_max"], _ = _q(rele)
     return out
 
 
@@ -72,20 +86,28 @@ def main():
     report = []
     for wl in ("h2air-1k", "h2air-1M", "hc36-256k", "hc36-front-2M"):
         mech, f, dt = synth.workload(wl)
-        fs = synth.subsample(f, sample(f, args.cells))
-        rho, e = P.initial_state(mech, fs)
         opts = dict(max_halvings=0) if wl == "h2air-1k" else {}
-        for prec, name, tol in ((chem.FP64, "fp64", P.TOL_FP64), (chem.MIXED, "mixed", P.TOL_MIXED)):
-            # the oracle under the path's own Newton control
-            ctl = P.MIXED_OPTS if name == "mixed" else {}
-            rr, er, oo = P.oracle_reference(mech, rho, e, dt, fs.T, threads=threads, **opts, **ctl)
-            c = chem.Chem(mech, precision=prec, **opts)
-            rg, eg, og = P.gpu_run(torch, c, rho, e, dt, T_in=fs.T)
-            c.close()
-            s = stats(rg, eg, og, rr, er, oo, rho)
-            s.update(workload=wl, precision=name, tolerance=tol)
-            report.append(s)
-            print(json.dumps(s), flush=True)
+        for part, idx in samples(f, args.cells).items():
+            fs = synth.subsample(f, idx)
+            rho, e = P.initial_state(mech, fs)
+            for prec, name, tol in ((chem.FP64, "fp64", P.TOL_FP64), (chem.MIXED, "mixed", P.TOL_MIXED)):
+                c = chem.Chem(mech, precision=prec, **opts)
+                rg, eg, og = P.gpu_run(torch, c, rho, e, dt, T_in=fs.T)
+                c.close()
+                rep = replay(mech, rho, e, dt, fs.T, og, threads, **opts)
+                # the oracle under the path's own Newton control, and (mixed)
+                # under the default control as well
+                ctls = [("own", P.MIXED_OPTS if name == "mixed" else {})]
+                if name == "mixed":
+                    ctls.append(("default", {}))
+                for ctl_name, ctl in ctls:
+                    rr, er, oo = P.oracle_reference(mech, rho, e, dt, fs.T, threads=threads, **opts, **ctl)
+                    for floor in (P.FLOOR, P.FLOOR_MIXED):
+                        s = stats(rho, rg, eg, og, rr, er, oo, rep, floor)
+                        s.update(workload=wl, sample=part, precision=name, tolerance=tol,
+                                 oracle_control=ctl_name, species_floor=floor)
+                        report.append(s)
+                        print(json.dumps(s), flush=True)
 
 
 if __name__ == "__main__":

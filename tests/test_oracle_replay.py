@@ -87,7 +87,7 @@ def test_replay_of_own_schedule_is_exact(oracle_mod, wl):
     fs = synth.subsample(f, idx)
     rho, e = om.state_from_tpy(fs.T, fs.P, fs.Y)
     for kappa in (0.0, 0.01):
-        r1, e1, o = om.advance_batch(rho, e, dt, T_in=fs.T, threads=4, schedule=True,
+        r1, e1, o = om.advance_batch(rho, e, dt, T_in=fs.T, threads=4, schedule=True, states_cap=32,
                                      opts=oracle_mod.default_opts(conv_kappa=kappa))
         assert (o["status"] == 0).all()
         if wl != "h2air-1M":
@@ -101,6 +101,19 @@ def test_replay_of_own_schedule_is_exact(oracle_mod, wl):
         assert (o2["status"] == 0).all()
         assert np.array_equal(r2, r1) and np.array_equal(e2, e1)
         assert np.array_equal(o2["T"], o["T"])
+        # guided by the oracle's own states after each accepted substep, each
+        # substep's Newton starts at (kappa = 0) or near (kappa > 0) its root
+        # and converges back to it within the tolerance
+        assert (o["substeps"] <= 32).all()
+        r3, e3, o3 = om.advance_batch_replay(rho, e, dt, o["schedule"], na, T_in=fs.T, threads=4,
+                                             opts=oracle_mod.replay_opts(), guides=o["states"])
+        assert (o3["status"] == 0).all()
+        rel = np.abs(r3 - r1) / np.maximum(np.abs(r1), 1e-12 * rho.sum(0)[None, :])
+        assert rel.max() <= 1e-10
+        np.testing.assert_allclose(o3["T"], o["T"], rtol=1e-12)
+        # the states the oracle recorded are its own: the last one is the result
+        last = o["states"][np.arange(len(na)), o["substeps"] - 1]
+        assert np.array_equal(last[:, :-1].T, r1) and np.array_equal(last[:, -1], e1)
 
 
 def test_replay_refuses_inconsistent_schedules(oracle_mod):
