@@ -68,10 +68,13 @@ struct Grp {
         return v;
     }
     __device__ __forceinline__ static int any(int v) {
-        if (G == 32) return __any_sync(kFull, v);
+        if constexpr (G == 32) {
+            return __any_sync(kFull, v);
+        } else {
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
-        return v;
+            for (int o = G / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
+            return v;
+        }
     }
     // maximum of non-negative doubles on the integer pipe (their bit
     // patterns order the same way; a NaN, whose bits are larger than any
@@ -79,18 +82,19 @@ struct Grp {
     // the low words of the lanes holding the high maximum
     __device__ __forceinline__ static double max_nonneg(double v) {
         unsigned long long b = (unsigned long long)__double_as_longlong(v);
-        if (G == 32) {
+        if constexpr (G == 32) {
             const unsigned hi = (unsigned)(b >> 32);
             const unsigned mhi = __reduce_max_sync(kFull, hi);
             const unsigned mlo = __reduce_max_sync(kFull, hi == mhi ? (unsigned)b : 0u);
             return __longlong_as_double((long long)(((unsigned long long)mhi << 32) | mlo));
-        }
+        } else {
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            const unsigned long long b2 = __shfl_xor_sync(kFull, b, o);
-            b = b2 > b ? b2 : b;
+            for (int o = G / 2; o > 0; o >>= 1) {
+                const unsigned long long b2 = __shfl_xor_sync(kFull, b, o);
+                b = b2 > b ? b2 : b;
+            }
+            return __longlong_as_double((long long)b);
         }
-        return __longlong_as_double((long long)b);
     }
     // largest key, lowest index on ties
     __device__ __forceinline__ static void argmax(unsigned long long &k, int &i) {
@@ -428,7 +432,7 @@ struct SlotMem {
     double *x, *x0, *c, *hRT, *es, *em, *emi, *Q, *part;
     int *ek;
     JT *D, *dTdr, *w, *u, *A, *dQdT, *qtb, *A1, *A2, *rhs;
-    JT *cJ, *hJ, *esJ;   // FP32 path: c, h/RT and e^sens in the Jacobian type
+    JT *cJ, *hJ, *esJ;   // FP32 path: c, h/RT and the energies e_s in the Jacobian type
     // layout and sizes in chem_internal.h (slot_bytes_for, slot_stride); the FP64 path has
     // no FP32 copies (cJ = c, hJ = hRT), the FP32 path no FP64 hRT, es or
     // dTdr.  The species values of the rates (c, the split exponentials em,
@@ -524,15 +528,19 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         sm.em[s] = ey;
         sm.emi[s] = frcp(ey);
         sm.ek[s] = eK;
-        const double es = RM * T * (hRT - 1.0) - __ldg(spr + 3);
         if (f32) {
-            sm.esJ[s] = to_jt<JT>(es);
+            // the species energy with its formation part, e_s = (R/M) T (h/RT
+            // - 1): the Jacobian's temperature column (-e_s dT/de) and the
+            // linearised temperature guess need no more, so FP32
+            const JT hJs = to_jt<JT>(hRT);
+            sm.esJ[s] = (JT)__ldg(m.spf + s * kSpStride + 2) * Tf * (hJs - (JT)1);
             const auto d = coef_row(m.tpoly_f, ns, s, rg);
             const float cv = fmaf(fmaf(fmaf(fmaf(d[4], Tf, d[3]), Tf, d[2]), Tf, d[1]), Tf, d[0]);
             rhocvf = fmaf(d2f_rz(xs), cv, rhocvf);
             sm.cJ[s] = to_jt<JT>(ci);
-            sm.hJ[s] = to_jt<JT>(hRT);
+            sm.hJ[s] = hJs;
         } else {
+            const double es = RM * T * (hRT - 1.0) - __ldg(spr + 3);
             const auto c = coef_row(m.tpoly, ns, s, rg);
             const double cv = fma(fma(fma(fma(c[10], T, c[9]), T, c[8]), T, c[7]), T, c[6]);
             rhocv = fma(xs, cv, rhocv);
@@ -593,8 +601,14 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         load_rxn(r + G);
         const int a0 = fr & 0xff, a1 = (fr >> 8) & 0xff, a2 = (fr >> 16) & 0xff;
         const int b0 = fpw & 0xff, b1 = (fpw >> 8) & 0xff, b2 = (fpw >> 16) & 0xff;
-        const double Pf = sm.c[a0] * sm.c[a1] * sm.c[a2];
-        const double Pb = sm.c[b0] * sm.c[b1] * sm.c[b2];
+        // third factor slots: the sentinel's factors are exactly 1 (0 for the
+        // enthalpies), so a pass none of whose reactions has a third factor on
+        // either side skips them, with bit-identical results (the 36-species
+        // mechanism has at most two per side); the vote makes the branch
+        // uniform, so the skipped FP64 products cost no pipe slot
+        const bool s3 = __any_sync(__activemask(), (a2 != ns) | (b2 != ns));
+        double Pf = sm.c[a0] * sm.c[a1];
+        double Pb = sm.c[b0] * sm.c[b1];
         const double lnkf = lnA + beta * lnT - EaR * invT;
         const double kf = fexp(lnkf, tab);
         // K_b = K_f / K_c with 1/K_c = (RT/P_a)^dnu exp(dG/RT) (Eq. 24) as
@@ -602,8 +616,16 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         // (products) and their inverses (reactants), the sentinel giving 1:
         // mantissas multiplied in FP64, powers of two added as integers, so no
         // exponential per reaction and no overflow in the partial products
-        const int K2 = (sm.ek[b0] + sm.ek[b1] + sm.ek[b2]) - (sm.ek[a0] + sm.ek[a1] + sm.ek[a2]);
-        const double Pm = ((sm.em[b0] * sm.em[b1]) * sm.em[b2]) * ((sm.emi[a0] * sm.emi[a1]) * sm.emi[a2]);
+        int K2 = (sm.ek[b0] + sm.ek[b1]) - (sm.ek[a0] + sm.ek[a1]);
+        double Pm;
+        if (s3) {
+            Pf *= sm.c[a2];
+            Pb *= sm.c[b2];
+            K2 = (sm.ek[b0] + sm.ek[b1] + sm.ek[b2]) - (sm.ek[a0] + sm.ek[a1] + sm.ek[a2]);
+            Pm = ((sm.em[b0] * sm.em[b1]) * sm.em[b2]) * ((sm.emi[a0] * sm.emi[a1]) * sm.emi[a2]);
+        } else {
+            Pm = (sm.em[b0] * sm.em[b1]) * (sm.emi[a0] * sm.emi[a1]);
+        }
         const double kb = scale_pow2(kf * Pm, K2);
         double CM = 1.0;
         const bool tb = (fr >> 24) & 1;
@@ -625,16 +647,21 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             sm.A1[r] = A1v;
             sm.A2[r] = A2v;
             if (r < m.ntb) sm.qtb[r] = to_jt<JT>(q);
-            const JT shf = (sm.hJ[b0] + sm.hJ[b1] + sm.hJ[b2]) - (sm.hJ[a0] + sm.hJ[a1] + sm.hJ[a2]);
+            const JT shf = s3 ? (sm.hJ[b0] + sm.hJ[b1] + sm.hJ[b2]) - (sm.hJ[a0] + sm.hJ[a1] + sm.hJ[a2])
+                              : (sm.hJ[b0] + sm.hJ[b1]) - (sm.hJ[a0] + sm.hJ[a1]);
             const JT dlnkf = (JT)__ldg(rf + 1) * iT * iT + (JT)__ldg(rf) * iT;
             const JT dlnKc = (shf - (JT)__ldg(rf + 2)) * iT;
             // concentration products again in FP32 (a conversion costs an
             // FP64-pipe slot, three FP32 products do not)
-            const JT PfJ = sm.cJ[a0] * sm.cJ[a1] * sm.cJ[a2];
-            const JT PbJ = sm.cJ[b0] * sm.cJ[b1] * sm.cJ[b2];
+            JT PfJ = sm.cJ[a0] * sm.cJ[a1], PbJ = sm.cJ[b0] * sm.cJ[b1];
+            if (s3) {
+                PfJ *= sm.cJ[a2];
+                PbJ *= sm.cJ[b2];
+            }
             sm.dQdT[r] = A1v * PfJ * dlnkf - A2v * PbJ * (dlnkf - dlnKc);
         } else {
-            const double sh = (sm.hRT[b0] + sm.hRT[b1] + sm.hRT[b2]) - (sm.hRT[a0] + sm.hRT[a1] + sm.hRT[a2]);
+            const double sh = s3 ? (sm.hRT[b0] + sm.hRT[b1] + sm.hRT[b2]) - (sm.hRT[a0] + sm.hRT[a1] + sm.hRT[a2])
+                                 : (sm.hRT[b0] + sm.hRT[b1]) - (sm.hRT[a0] + sm.hRT[a1]);
             if (r < m.ntb) sm.qtb[r] = (JT)q;
             sm.A1[r] = (JT)(CM * kf);
             sm.A2[r] = (JT)(CM * kb);
@@ -791,7 +818,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const int s = (meta.y >> 8) & 0xff, k = meta.y & 0xff;
         const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
         // (the reduced system's column k: dT/drho_k - e_f,k dT/de)
-        const JT dTdrk = f32 ? -(sm.esJ[k] + (JT)__ldg(m.spf + k * kSpStride + 3)) * (JT)dTdef : sm.dTdr[k];
+        const JT dTdrk = f32 ? -sm.esJ[k] * (JT)dTdef : sm.dTdr[k];
         JT J = f32 ? sm.w[s] * dTdrk : sm.w[s] * dTdrk + sm.u[s] * invMk;
         JT a0 = 0, a1 = 0;
         int e = meta.x, q = 0;
@@ -942,7 +969,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         if (f32) {
             df = (float)sm.A[i * ldA + N];
             d = f2d_alu(df);
-            desf -= (float)sm.esJ[i] * df;
+            desf -= (float)sm.esJ[i] * df;   // e_s with its formation part: see below
             sef = fmaf(__ldg(m.spf + i * kSpStride + 3), df, sef);
         } else {
             d = (double)sm.A[i * ldA + N];
@@ -964,8 +991,10 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             if (!finite_bits(xe)) nonfinite = 1;
             const double ri = ratio(de, fma(rtol, fabs(xe), atol_e));
             if (bits_gt(ri, nrm)) nrm = ri;
+            // dT = (de - sum_s e_s^sens drho_s) / (rho cv), where de = -R_E -
+            // e_f . drho: the FP32 path's e_s carry e_f, so it adds -R_E
             if (f32)
-                desf += d2f_rz(de);
+                desf += d2f_rz(-RE);
             else
                 des += de;
         }
