@@ -190,7 +190,8 @@ constexpr int kBlockHeaderBytes = 0;
 //             path hRT (double), ek (int), FP32 path cJ, hJ (float), then the
 //             per-reaction values dQdT, A1, A2 (nr JT each) and qtb (ntb JT);
 //             after the D entries: the augmented matrix ns x (ns+1) in JT
-//             (the energy unknown is eliminated)
+//             (the energy unknown is eliminated), FP64 row-major, FP32
+//             column-major with columns padded to a multiple of 4 rows
 __host__ __device__ inline long long align16(long long b) { return (b + 15) / 16 * 16; }
 
 #ifdef __CUDACC__
@@ -228,8 +229,9 @@ __host__ __device__ inline long long slot_dreg_bytes(int nr, int nD, int n_items
 }
 __host__ __device__ inline long long slot_union_bytes(int ns, int nr, int ntb, int jt) {
     const int n = ns + 1;
+    // the matrix: FP64 ns rows of n; FP32 n columns of ns rounded up to 4
     const long long a = slot_union_species_bytes(ns, jt) + 3LL * nr * jt + (long long)ntb * jt,
-                    b = (long long)ns * n * jt;
+                    b = jt == 8 ? (long long)ns * n * jt : (long long)n * ((ns + 3) & ~3) * jt;
     return align16(a > b ? a : b);
 }
 __host__ __device__ inline long long slot_bytes_for(const DeviceMech &m, int jt) {

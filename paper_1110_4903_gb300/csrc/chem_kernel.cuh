@@ -385,45 +385,51 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
     if (need) T_out = T;
 }
 
-// Trailing update a_ik -= a_ij (a_jk / a_jj) of elimination step j (i > j,
-// k > j, the augmented column included), organised by columns: a lane owns a
-// column, keeps a_jk / a_jj in a register and walks the rows four at a time,
-// so four independent updates are in flight and the a_ij are broadcast
+// FP32 trailing update a_ik -= a_ij (a_jk / a_jj) of elimination step j
+// (i > j, k > j, the right-hand side column n included) on the column-major
+// matrix A[k*ld + i], ld a multiple of 4.  A lane owns a column, keeps
+// a_jk / a_jj in a register and walks its rows four at a time with 16-byte
+// loads and stores; the a_ij of the pivot column are 16-byte broadcast
 // reads.  When fewer columns than lanes remain, the rows of each column are
-// split over 2, 4, ... lanes.  The multipliers are never stored: the
-// right-hand side is eliminated with the matrix, and back substitution reads
-// U only.
-template <int G, typename JT>
-__device__ __forceinline__ void lu_update_by_columns(JT *A, int lda, int n, int j, int sl, JT inv) {
-    const int C = n - j, R = n - j - 1;
-    if (R <= 0) return;
-    int kc = sl, i0 = j + 1, i1 = n;
+// split over 2, 4, ... lanes at multiples of four rows.  The multipliers are
+// never stored: the right-hand side is eliminated with the matrix, and back
+// substitution reads U only.  Each element gets fma(-a_ij, a_jk / a_jj, a_ik)
+// whichever lane computes it.
+template <int G>
+__device__ __forceinline__ void lu_update_colmajor(float *A, int ld, int n, int j, int sl, float inv) {
+    const int C = n - j, r0 = j + 1;
+    if (r0 >= n) return;
+    int kc = sl, i0 = r0, i1 = n;
     if (C < G) {
         const int lg = C > 1 ? 32 - __clz(C - 1) : 0;   // columns rounded up to 2^lg
         const int lgB = (__ffs(G) - 1) - lg;              // lanes per column, log2
-        const int rows = (R + (1 << lgB) - 1) >> lgB;
         kc = sl & ((1 << lg) - 1);
         if (kc >= C) return;
-        i0 = j + 1 + (sl >> lg) * rows;
-        i1 = min(n, i0 + rows);
+        const int part = sl >> lg, base = r0 & ~3;
+        const int rows = ((((n - base) + (1 << lgB) - 1) >> lgB) + 3) & ~3;
+        i0 = max(r0, base + part * rows);
+        i1 = min(n, base + (part + 1) * rows);
     }
-    const JT *cj = A + j;
+    const float *cj = A + j * ld;
 #pragma unroll 1
     for (int k = j + 1 + kc; k <= n; k += G) {
-        const JT ajk = A[j * lda + k] * inv;
-        JT *ck = A + k;
+        float *ck = A + k * ld;
+        const float ajk = ck[j] * inv;
         int i = i0;
 #pragma unroll 1
+        for (; i < i1 && (i & 3); ++i) ck[i] = fmaf(-cj[i], ajk, ck[i]);
+#pragma unroll 1
         for (; i + 4 <= i1; i += 4) {
-            const JT l0 = cj[i * lda], l1 = cj[(i + 1) * lda], l2 = cj[(i + 2) * lda], l3 = cj[(i + 3) * lda];
-            const JT v0 = ck[i * lda], v1 = ck[(i + 1) * lda], v2 = ck[(i + 2) * lda], v3 = ck[(i + 3) * lda];
-            ck[i * lda] = fma(-l0, ajk, v0);
-            ck[(i + 1) * lda] = fma(-l1, ajk, v1);
-            ck[(i + 2) * lda] = fma(-l2, ajk, v2);
-            ck[(i + 3) * lda] = fma(-l3, ajk, v3);
+            const float4 l = *reinterpret_cast<const float4 *>(cj + i);
+            float4 v = *reinterpret_cast<const float4 *>(ck + i);
+            v.x = fmaf(-l.x, ajk, v.x);
+            v.y = fmaf(-l.y, ajk, v.y);
+            v.z = fmaf(-l.z, ajk, v.z);
+            v.w = fmaf(-l.w, ajk, v.w);
+            *reinterpret_cast<float4 *>(ck + i) = v;
         }
 #pragma unroll 1
-        for (; i < i1; ++i) ck[i * lda] = fma(-cj[i * lda], ajk, ck[i * lda]);
+        for (; i < i1; ++i) ck[i] = fmaf(-cj[i], ajk, ck[i]);
     }
 }
 
@@ -496,7 +502,11 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     constexpr bool f32 = sizeof(JT) == 4;
     // the linear system solved: the species block, with the energy unknown
     // eliminated (phase 5)
-    const int N = ns, ldA = N + 1;
+    // the matrix: FP64 row-major with rows of N + 1 (the right-hand side
+    // last), FP32 column-major with columns of ldc rows (a multiple of 4, for
+    // the 16-byte accesses of its elimination; the right-hand side is column N)
+    const int N = ns, ldA = N + 1, ldc = (N + 3) & ~3;
+    auto ix = [&](int i, int k) -> int { return f32 ? k * ldc + i : i * ldA + k; };
     const double invT = frcp(T);
     const double lnT = log(T);
     const double lnPaRT = log(kPa / kR) - lnT;
@@ -803,7 +813,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     {
         const JT cRE = f32 ? mh * (JT)dTdef * d2f_rz(RE) : (JT)(-h * dTde * RE);
 #pragma unroll 1
-        for (int i = sl; i < N; i += G) sm.A[i * ldA + N] = fma(sm.w[i], cRE, sm.rhs[i]);
+        for (int i = sl; i < N; i += G) sm.A[ix(i, N)] = fma(sm.w[i], cRE, sm.rhs[i]);
     }
 
     // 6. the reduced system's -h J'_sk = -h (J_sk - w_s e_f,k dT/de)
@@ -858,11 +868,11 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             for (; q < len; ++q, e += G) a0 = fma((JT)__ldg(gl.j_c + e), Dv[__ldg(gl.j_d + e)], a0);
             J += a0 + a1;
         }
-        sm.A[s * ldA + k] = mh * J;
+        sm.A[ix(s, k)] = mh * J;
     }
     __syncwarp();
 #pragma unroll 1
-    for (int i = sl; i < N; i += G) sm.A[i * ldA + i] += (JT)1;
+    for (int i = sl; i < N; i += G) sm.A[ix(i, i)] += (JT)1;
     __syncwarp();
 
     // 7. Gaussian elimination with row partial pivoting on [A | -F]
@@ -875,7 +885,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         int bi = N;
 #pragma unroll 1
         for (int i = j + sl; i < N; i += G) {
-            const unsigned long long kk = abs_key(sm.A[i * ldA + j]);
+            const unsigned long long kk = abs_key(sm.A[ix(i, j)]);
             if (bi == N || kk > best) {
                 best = kk;
                 bi = i;
@@ -889,16 +899,16 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         if (bi != j && bi < N) {
 #pragma unroll 1
             for (int k = j + sl; k <= N; k += G) {
-                const JT t = sm.A[j * ldA + k];
-                sm.A[j * ldA + k] = sm.A[bi * ldA + k];
-                sm.A[bi * ldA + k] = t;
+                const JT t = sm.A[ix(j, k)];
+                sm.A[ix(j, k)] = sm.A[ix(bi, k)];
+                sm.A[ix(bi, k)] = t;
             }
         }
         __syncwarp();
         // (the FP64 pivot takes the full-precision reciprocal: a 1e-14 error
         // in every multiplier reaches the trace species of ill-conditioned
         // cells at 1e-10)
-        const JT inv = frcp(sm.A[j * ldA + j]);
+        const JT inv = frcp(sm.A[ix(j, j)]);
         if (!f32) {
 #pragma unroll 1
             for (int i = j + 1 + sl; i < N; i += G) sm.A[i * ldA + j] *= inv;
@@ -908,7 +918,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         if (f32) {
             // FP32: bound by issue and latency, not by the pipe; the update
             // reads column j unscaled and never A[j][j]
-            lu_update_by_columns<G, JT>(sm.A, ldA, N, j, sl, inv);
+            lu_update_colmajor<G>(reinterpret_cast<float *>(sm.A), ldc, N, j, sl, (float)inv);
         } else {
             // FP64: a flat walk over the trailing elements keeps every lane of
             // every FP64 instruction busy (a masked lane costs a full slot)
@@ -935,17 +945,17 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         }
         __syncwarp();
         // FP32: the reciprocal replaces the pivot once every lane has read it
-        if (f32 && sl == 0) sm.A[j * ldA + j] = inv;
+        if (f32 && sl == 0) sm.A[ix(j, j)] = inv;
     }
     __syncwarp();
     // back substitution, U delta = y
 #pragma unroll 1
     for (int j = N - 1; j >= 0; --j) {
-        const JT dj = sm.A[j * ldA + N] * sm.A[j * ldA + j];
+        const JT dj = sm.A[ix(j, N)] * sm.A[ix(j, j)];
         __syncwarp();
-        if (sl == 0) sm.A[j * ldA + N] = dj;
+        if (sl == 0) sm.A[ix(j, N)] = dj;
 #pragma unroll 1
-        for (int i = sl; i < j; i += G) sm.A[i * ldA + N] -= sm.A[i * ldA + j] * dj;
+        for (int i = sl; i < j; i += G) sm.A[ix(i, N)] -= sm.A[ix(i, j)] * dj;
         __syncwarp();
     }
 
@@ -967,12 +977,12 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         float df = 0.f;
         double d;
         if (f32) {
-            df = (float)sm.A[i * ldA + N];
+            df = (float)sm.A[ix(i, N)];
             d = f2d_alu(df);
             desf -= (float)sm.esJ[i] * df;   // e_s with its formation part: see below
             sef = fmaf(__ldg(m.spf + i * kSpStride + 3), df, sef);
         } else {
-            d = (double)sm.A[i * ldA + N];
+            d = (double)sm.A[ix(i, N)];
             des -= sm.es[i] * d;
             se = fma(__ldg(m.sp + i * kSpStride + 3), d, se);
         }
