@@ -359,6 +359,12 @@ int chem_batched_solve(int32_t method, int32_t n, int64_t n_sys, double *A, doub
 int chem_selftest_math(int64_t n, const double *x, double *y_exp, double *y_exp_ref,
                        double *y_rcp, double *y_rcp_ref, void *stream);
 
+/* Diagnostics: the step kernel's logarithm of the temperature (table-driven,
+ * after Tang, ACM TOMS 16(4), 1990) at n device points x (finite, >= 2: its
+ * domain; the kernels take it of T in [200, 6000] K), next to CUDA's log.
+ * Synchronous. */
+int chem_selftest_log(int64_t n, const double *x, double *y_log, double *y_log_ref, void *stream);
+
 /* Diagnostics for the equilibrium constants' exponent arithmetic (Eq. 24 as
  * the kernels form it): at n device points, exp(x[i]) split into a mantissa
  * y_mant[i] in [0.99, 2.01] and a power of two y_pow[i] (|x| >= 2^22 and

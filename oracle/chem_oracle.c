@@ -496,8 +496,10 @@ static int be_substep(const om_mech *m, const om_opts *o, const double *x0, doub
             ok = 1;
             break;
         }
+        /* theta / (1 - theta) norm <= kappa with theta = norm / norm_prev in
+         * [0, 1), multiplied by (1 - theta) norm_prev > 0 */
         if (o->conv_kappa > 0.0 && k >= 1 && norm < norm_prev &&
-            norm / norm_prev / (1.0 - norm / norm_prev) * norm <= o->conv_kappa) {
+            norm * norm <= o->conv_kappa * (norm_prev - norm)) {
             ok = 1;
             break;
         }

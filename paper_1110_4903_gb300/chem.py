@@ -124,6 +124,7 @@ def lib():
             "chem_server_stats": [p, p],
             "chem_batched_solve": [i32, i32, i64, p, p, p, p, p],
             "chem_selftest_math": [i64, p, p, p, p, p, p],
+            "chem_selftest_log": [i64, p, p, p, p],
             "chem_selftest_scaled_exp": [i64, p, p, p, p, p, p, p],
         }
         for name, args in sig.items():

@@ -164,7 +164,7 @@ static void third_body_first(const chem_mech_desc *in, ReorderedMech &o) {
 
 // Derived tables (layouts in chem_internal.h)
 struct HostTables {
-    std::vector<double> thermo, tmid, tpoly, sp, rxn_d, eff_c, d_c, j_c, exp_tab;
+    std::vector<double> thermo, tmid, tpoly, sp, rxn_d, eff_c, d_c, j_c, exp_tab, log_tab;
     std::vector<unsigned> div16;
     std::vector<float> tpoly_f;
     std::vector<float> rxn_df, d_cef, spf;
@@ -181,6 +181,17 @@ struct HostTables {
     } lay[kLayouts];
     int nD = 0, nD_F = 0, nD_B = 0, nD_FB = 0, nJ = 0, n_items = 0, ntb = 0;
 };
+
+// {1/F, ln F} at F = 1 + j/kLogTab, j = 0..kLogTab, rounded from extended
+// precision (the table of the kernels' logarithm)
+void fill_log_table(std::vector<double> &tab) {
+    tab.resize(2 * (kLogTab + 1));
+    for (int j = 0; j <= kLogTab; ++j) {
+        const long double F = 1.0L + (long double)j / kLogTab;
+        tab[2 * j] = (double)(1.0L / F);
+        tab[2 * j + 1] = (double)std::log(F);
+    }
+}
 
 static void build_tables(const chem_mech_desc *d, HostTables &t) {
     const int ns = d->n_species, nr = d->n_reactions;
@@ -389,6 +400,7 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     for (int c = 1; c <= 66; ++c) t.div16[c] = (65536u + c - 1) / c;
     t.exp_tab.resize(kExpTab);
     for (int j = 0; j < kExpTab; ++j) t.exp_tab[j] = (double)std::exp2l((long double)j / kExpTab);
+    fill_log_table(t.log_tab);
     // FP32 copies for the mixed-precision Jacobian
     t.rxn_df.assign((size_t)nr * kRxnDStride, 0.0f);
     for (int r = 0; r < nr; ++r) {
@@ -531,7 +543,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
                  i_rf = addv(t.rxn_f), i_ep = addv(t.eff_ptr), i_es = addv(t.eff_sp), i_ec = addv(t.eff_c),
                  i_dpk = addv(t.d_pk), i_dc = addv(t.d_c), i_sip = addv(t.sp_item_ptr),
                  i_ex = addv(t.exp_tab), i_div = addv(t.div16), i_rdf = addv(t.rxn_df), i_dcef = addv(t.d_cef),
-                 i_spf = addv(t.spf);
+                 i_spf = addv(t.spf), i_log = addv(t.log_tab);
     size_t i_lay[kLayouts][8];
     for (int li = 0; li < kLayouts; ++li) {
         const auto &L = t.lay[li];
@@ -592,6 +604,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     m.d_cef = (const float *)at(i_dcef);
 
     m.spf = (const float *)at(i_spf);
+    m.log_tab = (const double2 *)at(i_log);
     return CHEM_OK;
 }
 

@@ -66,5 +66,6 @@ int launch_step(Handle *h, const chem_advance_args *a, int prec, int G, unsigned
 int launch_cfg(Handle *h, const chem_advance_args *a, int prec, const LaunchCfg *cfg,
                unsigned long long *counter);
 unsigned long long *next_counter(Handle *h);
+void fill_log_table(std::vector<double> &tab);
 void destroy_serving(Handle *h);
 }  // namespace chem

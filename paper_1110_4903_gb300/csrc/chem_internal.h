@@ -16,6 +16,7 @@ namespace chem {
 constexpr double kR = 8.314462618;     // universal gas constant, J/(mol K)
 constexpr double kPa = 101325.0;       // standard pressure in K_e (Eq. 24), Pa
 constexpr double kTref = 298.15;       // reference of the formation energies, K
+constexpr double kLnPaOverR = 9.408091968961747;   // ln(kPa / kR), rounded from 40 digits
 constexpr double kTlo = 200.0;         // temperature-recovery bracket, K
 constexpr double kThi = 6000.0;
 constexpr int kTmaxIter = 50;          // temperature-recovery iterations
@@ -66,6 +67,8 @@ constexpr int kMaxBlockThreads = 320;
 
 // Entries of the exp table (2^(j/kExpTab)).
 constexpr int kExpTab = 256;
+// Intervals of the log table: kLogTab + 1 entries {1/F, ln F}, F = 1 + j/kLogTab.
+constexpr int kLogTab = 128;
 
 // D entries: one per (reaction r, species k) pair whose concentration the
 // progress rate Q_r depends on, holding dQ_r/drho_k without the all-ones
@@ -130,6 +133,7 @@ struct DeviceMech {
     GatherLayout gl[kLayouts];
     const int *sp_item_ptr;     // [ns+1] work items of each species
     const double *exp_tab;      // [kExpTab] 2^(j/kExpTab)
+    const double2 *log_tab;     // [kLogTab + 1] {1/F, ln F}, F = 1 + j/kLogTab
     const unsigned *div16;      // [67] ceil(2^16 / c): x / c = (x div16[c]) >> 16 for x < 64
     // FP32 copies for the mixed-precision Jacobian
     const float *rxn_df;        // [nr][4] beta, Ea/R, sum nu, 0

@@ -304,6 +304,33 @@ __device__ __forceinline__ double scale_pow2(double v, int k) {
     return __longlong_as_double(b + ((long long)k << 52));
 }
 
+// ln x for x >= 2 by the table-driven reduction of P. T. P. Tang, ACM TOMS
+// 16(4), 1990: x = 2^k y with y in [1, 2), F = 1 + j/128 the table point
+// nearest to y (j = 0..128), f = y - F (exact, |f| <= 2^-8), u = f (1/F),
+// and ln x = k ln2 + ln F + ln(1 + u) with ln(1 + u) by its series to u^6
+// (truncation below 2^-56 / 7): ten FP64 operations, within 1.5 ulp.  {1/F,
+// ln F} come from a table; k becomes a double on the integer pipe.  (Below 2
+// the result can be small next to k ln2 + ln F, and the table's rounding
+// then leaves an absolute error near 1e-16.  The kernels take it of T in
+// [200, 6000] K.)
+__device__ __forceinline__ double flog(double x, const double2 *tab) {
+    const long long b = __double_as_longlong(x);
+    const int k = (int)(b >> 52) - 1023;
+    const double y = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const int j = (int)((b >> 45) & 0x7f) + (int)((b >> 44) & 1);
+    const double F = __longlong_as_double(0x3ff0000000000000LL + ((long long)j << 45));
+    const double2 t = __ldg(tab + j);
+    const double u = (y - F) * t.x;
+    double p = fma(u, -1.0 / 6.0, 0.2);
+    p = fma(u, p, -0.25);
+    p = fma(u, p, 1.0 / 3.0);
+    p = fma(u, p, -0.5);
+    p = fma(u, p, 1.0);
+    // k as a double: added to the bit pattern of 1.5 * 2^52, whose ulp is 1
+    const double kd = __longlong_as_double(0x4338000000000000LL + k) - 6755399441055744.0;
+    return fma(u, p, fma(kd, 0.6931471805599453, t.y));
+}
+
 // NASA-7 entropy from the thermo coefficients of one species and range
 // (layout in chem_internal.h)
 __device__ __forceinline__ double nasa_s(const CoefRow<double> &th, double T, double lnT) {
@@ -375,9 +402,10 @@ __device__ __forceinline__ void recover_T(const DeviceMech &m, const double *x, 
                 if (!(bits_gt(Tn, lo) && bits_lt(Tn, hi))) Tn = 0.5 * (lo + hi);
                 const double dT = Tn - T;
                 T = Tn;
-                if (fabs(dT) <= kTtol * T) {
+                // (comparisons of non-negative doubles on their bit patterns)
+                if (!bits_gt(fabs(dT), kTtol * T)) {
                     done = true;
-                    ok = !(T <= kTlo * (1.0 + 1e-9) || T >= kThi * (1.0 - 1e-9));
+                    ok = bits_gt(T, kTlo * (1.0 + 1e-9)) && bits_lt(T, kThi * (1.0 - 1e-9));
                 }
             }
         }
@@ -508,8 +536,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     const int N = ns, ldA = N + 1, ldc = (N + 3) & ~3;
     auto ix = [&](int i, int k) -> int { return f32 ? k * ldc + i : i * ldA + k; };
     const double invT = frcp(T);
-    const double lnT = log(T);
-    const double lnPaRT = log(kPa / kR) - lnT;
+    const double lnT = flog(T, m.log_tab);   // T in [200, 6000] K: normal
+    const double lnPaRT = kLnPaOverR - lnT;
 
     // 1. concentrations and thermodynamics (species); the heat capacity only
     //    feeds dT/drho, dT/de and the next temperature guess, so the FP32
@@ -1136,7 +1164,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
             int neg = 0;
 #pragma unroll 1
             for (int i = sl; i < ns; i += G)
-                if (sm.x[i] < -atol_rho) neg = 1;
+                if (bits_lt(sm.x[i], 0.0) && bits_gt(fabs(sm.x[i]), atol_rho)) neg = 1;   // x < -atol
             neg = Grp<G>::any(neg);
             __syncwarp();
             if (state == kInitT) {
@@ -1222,15 +1250,17 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
         newton_iteration<G, JT>(m, tab, sm, sl, T, h, atol_rho, atol_e, o.rtol, norm, bad, T_pred);
         if (state == kNewtonReady) {
             // start the next temperature recovery from the linear prediction
-            if (T_pred > kTlo && T_pred < kThi) T = T_pred;
+            if (bits_gt(T_pred, kTlo) && bits_lt(T_pred, kThi)) T = T_pred;
             ++iters;
             if (bad) {
                 substep_fail();
-            } else if (o.point_implicit || norm <= 1.0 ||
-                       (o.conv_kappa > 0.0 && k >= 1 && norm < norm_prev &&
-                        norm / norm_prev / (1.0 - norm / norm_prev) * norm <= o.conv_kappa)) {
+            } else if (o.point_implicit || !bits_gt(norm, 1.0) ||
+                       (o.conv_kappa > 0.0 && k >= 1 && bits_lt(norm, norm_prev) &&
+                        norm * norm <= o.conv_kappa * (norm_prev - norm))) {
+                // (the contraction-rate stop theta / (1 - theta) norm <= kappa,
+                // theta = norm / norm_prev < 1, multiplied out: no division)
                 state = kCheckT;
-            } else if (o.div_check && k >= 2 && norm >= norm_prev) {
+            } else if (o.div_check && k >= 2 && !bits_lt(norm, norm_prev)) {
                 substep_fail();
             } else {
                 norm_prev = norm;

@@ -1,6 +1,7 @@
-// chem_selftest.cu -- diagnostics: the step kernel's own exp and reciprocal
-// evaluated next to CUDA's, and its split exponential and power-of-two
-// scaling, so tests can bound their error and check their range handling.
+// chem_selftest.cu -- diagnostics: the step kernel's own exp, logarithm and
+// reciprocal evaluated next to CUDA's, and its split exponential and
+// power-of-two scaling, so tests can bound their error and check their range
+// handling.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -35,9 +36,38 @@ __global__ void selftest_scaled_exp_kernel(long long n, const double *x, const d
     y_scaled[i] = scale_pow2(v[i], k[i]);
 }
 
+// (flog's domain is x >= 2: see its comment)
+__global__ void selftest_log_kernel(long long n, const double *x, const double2 *tab, double *y_log,
+                                    double *y_log_ref) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    y_log[i] = flog(x[i], tab);
+    y_log_ref[i] = log(x[i]);
+}
+
 }  // namespace chem
 
 using namespace chem;
+
+extern "C" int chem_selftest_log(int64_t n, const double *x, double *y_log, double *y_log_ref, void *stream) {
+    if (n < 0 || !x || !y_log || !y_log_ref) return fail(CHEM_E_INVALID_ARG, "NULL argument");
+    if (n == 0) return CHEM_OK;
+    std::vector<double> tab;
+    fill_log_table(tab);
+    double *d_tab = nullptr;
+    cudaError_t ce = cudaMalloc(&d_tab, sizeof(double) * tab.size());
+    if (ce != cudaSuccess) return fail(CHEM_E_OOM, "self-test table");
+    ce = cudaMemcpy(d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+        selftest_log_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            n, x, reinterpret_cast<const double2 *>(d_tab), y_log, y_log_ref);
+        ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize((cudaStream_t)stream);
+    }
+    cudaFree(d_tab);
+    if (ce != cudaSuccess) return cuda_fail(ce, "self-test");
+    return CHEM_OK;
+}
 
 static int upload_exp_table(double **d_tab) {
     std::vector<double> tab(kExpTab);

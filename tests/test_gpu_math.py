@@ -1,6 +1,6 @@
-"""The step kernel's own exp and reciprocal against CUDA's exp and IEEE
-division: at most 2 ulp apart on the ranges the rates use, identical on the
-special values."""
+"""The step kernel's own exp, logarithm and reciprocal against CUDA's exp,
+log and IEEE division: at most 2 ulp apart on the ranges the rates use,
+identical on the special values."""
 import numpy as np
 import pytest
 
@@ -107,3 +107,31 @@ def test_split_exponential_and_scaling():
     assert np.all(np.isinf(ys[over])) and np.array_equal(np.sign(ys[over]), np.sign(vals[over]))
     keep = ~normal
     assert np.array_equal(ys[keep], vals[keep], equal_nan=True)
+
+
+def test_log_of_temperatures():
+    """The kernels' table-driven logarithm (Tang's method) within 2 ulp of
+    CUDA's log and of the host's, on the temperature-recovery bracket and
+    across its domain x >= 2, including table points and midpoints."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1110_4903_gb300 import chem
+    rng = np.random.default_rng(2)
+    j = np.arange(129)
+    x = np.concatenate([rng.uniform(200.0, 6000.0, 300000),
+                        np.exp(rng.uniform(np.log(2.0), 700.0, 100000)),
+                        rng.uniform(2.0, 2.01, 20000),
+                        (1.0 + j / 128.0) * 1024.0, (1.0 + (j + 0.5) / 128.0) * 256.0,
+                        (1.0 + (j + 0.5) / 128.0) * 2.0, np.array([2.0, 200.0, 6000.0, 2.0 ** 1020])])
+    dev = torch.device("cuda")
+    xd = torch.tensor(x, device=dev)
+    y, yr = torch.empty_like(xd), torch.empty_like(xd)
+    assert chem.lib().chem_selftest_log(len(x), xd.data_ptr(), y.data_ptr(), yr.data_ptr(), None) == 0
+    y, yr = y.cpu().numpy(), yr.cpu().numpy()
+    for ref in (yr, np.log(x)):
+        ulp = np.abs(y - ref) / np.spacing(np.abs(ref))
+        w = int(np.argmax(ulp))
+        assert ulp.max() <= 2.0, (ulp.max(), x[w], y[w], ref[w])
