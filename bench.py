@@ -280,7 +280,7 @@ def time_path(torch, ch, rho0, e0, T_in, dt, precision, steps, warmup, flush, st
 
 
 def serving_run(torch, chem, synth, device, n_requests, rate_frac=0.7, budget_bytes=0, seed=5,
-                n_sims=128, max_inflight=8):
+                n_sims=128, max_inflight=64):
     """Poisson stream of chemistry requests from many simulations (9 or 36
     species with probability 1/2, 1k-256k cells log-uniform, dt log-uniform
     1e-8..1e-5 s) against a request server; states are resident on the
@@ -354,11 +354,12 @@ def serving_run(torch, chem, synth, device, n_requests, rate_frac=0.7, budget_by
         time.sleep(0.0002)
     wall = time.perf_counter() - t_start
     # latency from the scheduled arrival (server clock offset from the submit stamp)
-    lat = []
+    lat, wait = [], []
     for t, r, n in done:
         if t in arrivals:
             lat.append(r.t_done - r.t_submit + max(0.0, arrivals[t]))
-    lat = np.array(lat)
+            wait.append(r.t_start - r.t_submit)
+    lat, wait = np.array(lat), np.array(wait)
     st = srv.stats()
     srv.close()
     for h in handles:
@@ -366,8 +367,69 @@ def serving_run(torch, chem, synth, device, n_requests, rate_frac=0.7, budget_by
     return {"requests": len(lat), "rate_rps": rate, "capacity_rps": cap_rps, "rate_frac": rate_frac,
             "cell_updates_per_s": cells / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "admission_wait_p99_ms": float(np.percentile(wait, 99) * 1e3),
+            "requests_waiting_over_1ms": int((wait > 1e-3).sum()),
             "budget_bytes": st["budget_bytes"], "max_inflight": max_inflight,
-            "failed": st["failed"]}
+            "kernel_instances_launched": st["launches"], "failed": st["failed"]}
+
+
+def serving_background(torch, chem, synth, device, n_small=48, seed=7):
+    """Small requests arriving while a large one runs: one 2^18-cell request
+    of the 36-species mechanism, then n_small requests (1k-16k cells, 9 or
+    36 species alternately, dt 1e-6 s) at Poisson times spread over the large
+    request's own duration.  Reports the small requests' latency (submit to
+    done, host clock) and device span (first claim to last cell, device
+    clock), and the large request's span alone and in the mix."""
+    rng = np.random.default_rng(seed)
+    mechs = {9: synth.h2_air_9sp(), 36: synth.hydrocarbon_36sp()}
+    hs = {k: chem.Chem(m, precision=chem.MIXED) for k, m in mechs.items()}
+
+    def state(k, n, sd):
+        f = synth.uniform_field(mechs[k].ns, n, 900.0, 2800.0, seed=sd)
+        rho = torch.empty((mechs[k].ns, n), dtype=torch.float64, device=device)
+        e = torch.empty(n, dtype=torch.float64, device=device)
+        hs[k].state_from_tpy(torch.tensor(f.T, device=device), torch.tensor(f.P, device=device),
+                             torch.tensor(f.Y, device=device), rho, e)
+        return rho, e
+
+    big = state(36, 1 << 18, 20_000)
+    smalls = [(k, state(k, int(np.exp(rng.uniform(np.log(1024), np.log(16384)))), 20_001 + i))
+              for i, k in enumerate([9, 36] * (n_small // 2))]
+    torch.cuda.synchronize()
+    srv = chem.Server()
+    r, e = big[0].clone(), big[1].clone()
+    res = srv.wait(srv.submit(hs[36], r, e, 1e-6))
+    span_alone = (res.dev_last_ns - res.dev_first_ns) * 1e-9
+    gaps = rng.exponential(0.8 * span_alone / n_small, n_small)
+    r, e = big[0].clone(), big[1].clone()
+    tb = srv.submit(hs[36], r, e, 1e-6)
+    t0 = time.perf_counter()
+    tickets = []
+    for (k, (rs, es)), at in zip(smalls, np.cumsum(gaps)):
+        while time.perf_counter() - t0 < at:
+            time.sleep(0.0002)
+        tickets.append(srv.submit(hs[k], rs, es, 1e-6))
+    rb = srv.wait(tb)
+    lat, span, before = [], [], 0
+    for t in tickets:
+        q = srv.wait(t)
+        lat.append(q.t_done - q.t_submit)
+        span.append((q.dev_last_ns - q.dev_first_ns) * 1e-9)
+        before += q.dev_last_ns < rb.dev_last_ns
+    st = srv.stats()
+    srv.close()
+    for h in hs.values():
+        h.close()
+    lat, span = np.array(lat), np.array(span)
+    return {"large_cells": 1 << 18, "small_requests": n_small,
+            "small_p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "small_p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "small_device_span_p50_ms": float(np.percentile(span, 50) * 1e3),
+            "small_device_span_p99_ms": float(np.percentile(span, 99) * 1e3),
+            "small_finished_before_large": int(before),
+            "large_span_alone_ms": span_alone * 1e3,
+            "large_span_in_mix_ms": (rb.dev_last_ns - rb.dev_first_ns) * 1e-6,
+            "kernel_instances_launched": st["launches"], "failed": st["failed"]}
 
 
 def serving_sweep(args):
@@ -383,11 +445,14 @@ def serving_sweep(args):
     runs = []
     for frac in (0.5, 0.8, 1.0, 1.3):
         runs.append(serving_run(torch, chem, synth, device, args.serving_requests, frac, 0))
-    # the largest request (2^18 cells, 36 species) holds about 80 MB
-    for budget in (256 << 20, 96 << 20):
+    # the largest request (2^18 cells, 36 species) holds about 81 MB: at 90
+    # MiB no two large requests are in flight together, so admission waits
+    for budget in (256 << 20, 90 << 20):
         runs.append(serving_run(torch, chem, synth, device, args.serving_requests, 0.7, budget))
+    bg = serving_background(torch, chem, synth, device)
     print(json.dumps({"metric": "request latency of the chemistry server (Poisson arrivals)",
-                      "unit": "ms", "requests_per_run": args.serving_requests, "runs": runs}), flush=True)
+                      "unit": "ms", "requests_per_run": args.serving_requests, "runs": runs,
+                      "small_requests_during_a_large_one": bg}), flush=True)
 
 
 def main():
@@ -549,6 +614,7 @@ def main():
     if args.serving_requests > 0 and not args.cells:
         serving = serving_run(torch, chem, synth, device, args.serving_requests, args.serving_rate,
                               args.serving_budget)
+        serving["small_requests_during_a_large_one"] = serving_background(torch, chem, synth, device)
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -257,18 +257,26 @@ int chem_get_lanes_per_cell(chem_handle_t h, int32_t precision, int32_t *lanes);
 int chem_launch_count(chem_handle_t h, int64_t *count);
 
 /* ---- serving: continuous batching of requests from many simulations ----
- * A server owns a scheduler thread, max_inflight CUDA streams and a device
- * pool of hbm_budget_bytes.  chem_submit queues a request (its own mechanism
- * handle, cell count, dt and state); the scheduler admits the head of the
- * FIFO queue as soon as a stream is free and the request's bytes
- * (n_cells * (8 N_s + 20) + 1024) fit in the remaining budget, and runs it
- * on that stream, so requests admitted while others run overlap with them
- * on the device.  Device-resident states (host = 0) are stepped in place and
- * count against the budget while in flight; host states (host = 1) are
- * copied through the pool and back.  A request is computed exactly as by
+ * A server owns a scheduler thread, a device pool of hbm_budget_bytes and,
+ * per (handle, precision) its requests use, a lane: a ring of request
+ * descriptors in host memory mapped into the device's address space and
+ * persistent instances of the step kernel that claim the ring's cells.
+ * chem_submit queues a request (its own mechanism handle, cell count, dt and
+ * state); the scheduler admits the head of the FIFO queue when fewer than
+ * max_inflight requests are admitted and unfinished and its bytes
+ * (n_cells * (8 N_s + 20) + 1024) fit in the remaining budget, and publishes
+ * its cells to its lane.  Slots of a running kernel that free up claim the
+ * next published cell of whichever request comes next, so a request admitted
+ * while others run is stepped inside the same grid, cells of several requests
+ * in flight together on every SM (continuous batching on the device).  Lanes
+ * of different mechanisms share the GPU: each lane with work gets an equal
+ * share of its full grid.  Device-resident states (host = 0) are stepped in
+ * place and count against the budget while in flight; host states (host = 1)
+ * are copied through the pool and back.  A request is computed exactly as by
  * chem_advance_ex with the same handle, whatever else is in flight.
  * Requests larger than the whole budget are refused (CHEM_E_OVER_BUDGET).
- * Handles must outlive their requests. */
+ * Handles must outlive their requests; the server keeps a lane per handle
+ * used until it is destroyed. */
 #define CHEM_REQ_QUEUED    0
 #define CHEM_REQ_RUNNING   1
 #define CHEM_REQ_DONE      2
@@ -279,7 +287,7 @@ typedef struct chem_server_s *chem_server_t;
 
 typedef struct chem_server_options {
     int64_t hbm_budget_bytes;   /* device pool and in-flight budget; 0 = a quarter of free memory */
-    int32_t max_inflight;       /* requests running at once (streams), 1..64; default 8 */
+    int32_t max_inflight;       /* requests admitted and unfinished at once, 1..1023; default 64 */
     int32_t queue_capacity;     /* queued requests before chem_submit refuses; default 100000 */
 } chem_server_options;
 
@@ -304,11 +312,19 @@ typedef struct chem_result {
     int32_t state;              /* CHEM_REQ_* */
     int32_t error;              /* CHEM_E_* when FAILED */
     double  t_submit, t_start, t_done;   /* seconds on the server's monotonic clock */
+    uint64_t dev_first_ns;      /* device clock (globaltimer, ns) when the first of the request's
+                                   cells was claimed by a slot of a server kernel, */
+    uint64_t dev_last_ns;       /* and when its last cell finished (DONE requests; else 0) */
 } chem_result;
 
 typedef struct chem_server_stats_t {
-    int64_t queued, running, completed, failed;
-    int64_t bytes_in_use, budget_bytes, launches;
+    int64_t queued;             /* submitted, not yet admitted */
+    int64_t running;            /* admitted, not finished */
+    int64_t completed, failed;
+    int64_t bytes_in_use, budget_bytes;
+    int64_t launches;           /* server kernel instances launched so far */
+    int64_t kernel_instances;   /* server kernel instances on the device now */
+    int64_t queue_errors;       /* nonzero if a kernel failed to find a claimed cell's request */
 } chem_server_stats_t;
 
 int chem_server_default_options(chem_server_options *o);

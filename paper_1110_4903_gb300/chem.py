@@ -71,13 +71,14 @@ class Request(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("t_submit", C.c_double),
-                ("t_start", C.c_double), ("t_done", C.c_double)]
+                ("t_start", C.c_double), ("t_done", C.c_double), ("dev_first_ns", C.c_uint64),
+                ("dev_last_ns", C.c_uint64)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("queued", C.c_int64), ("running", C.c_int64), ("completed", C.c_int64),
                 ("failed", C.c_int64), ("bytes_in_use", C.c_int64), ("budget_bytes", C.c_int64),
-                ("launches", C.c_int64)]
+                ("launches", C.c_int64), ("kernel_instances", C.c_int64), ("queue_errors", C.c_int64)]
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
@@ -318,7 +319,7 @@ class Chem:
 class Server:
     """Request server (chem_server_*): continuous batching of chemistry steps."""
 
-    def __init__(self, budget_bytes=0, max_inflight=8, queue_capacity=100000):
+    def __init__(self, budget_bytes=0, max_inflight=64, queue_capacity=100000):
         o = ServerOptions()
         check(lib().chem_server_default_options(C.byref(o)))
         o.hbm_budget_bytes = int(budget_bytes)

@@ -611,8 +611,8 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
 // Launch shape of the backward-Euler kernel for (precision, G, warps per
 // block): wpb = 0 picks the warps per block and blocks per SM that maximise
 // resident warps within shared memory and registers.
-int configure(Handle *h, int prec, int G, int wpb_req, LaunchCfg &cfg) {
-    const void *fn = prec == CHEM_MIXED ? be_kernel_mixed(G) : be_kernel_fp64(G);
+int configure(Handle *h, int prec, int G, int wpb_req, LaunchCfg &cfg, bool queue) {
+    const void *fn = queue ? be_kernel_queue(prec, G) : prec == CHEM_MIXED ? be_kernel_mixed(G) : be_kernel_fp64(G);
     if (!fn) return fail(CHEM_E_INVALID_ARG, "lanes_per_cell %d not available", G);
     const int S = 32 / G;
     const long long sb = slot_stride(h->mech, prec == CHEM_MIXED ? 4 : 8, G);
@@ -654,14 +654,14 @@ int default_lanes(int ns, int prec) {
     return 32;
 }
 
-int get_cfg(Handle *h, int prec, int G, LaunchCfg **out) {
+int get_cfg(Handle *h, int prec, int G, LaunchCfg **out, bool queue) {
     const int wpb = G == h->lanes[prec] ? h->wpb[prec] : 0;
-    const int key = (prec * 64 + G) * 16 + wpb;
+    const int key = ((queue ? 2 : 0) + prec) * 64 * 16 + G * 16 + wpb;
     std::lock_guard<std::mutex> lk(h->mu);
     auto it = h->cfgs.find(key);
     if (it == h->cfgs.end()) {
         LaunchCfg c;
-        int rc = configure(h, prec, G, wpb, c);
+        int rc = configure(h, prec, G, wpb, c, queue);
         if (rc) return rc;
         it = h->cfgs.emplace(key, c).first;
     }
@@ -746,17 +746,21 @@ int launch_step(Handle *h, const chem_advance_args *a, int prec, int G, unsigned
     return launch_cfg(h, a, prec, cfg, counter);
 }
 
+StepOptions step_options(const Handle *h, int prec) {
+    return StepOptions{h->opts.rtol, h->opts.atol_rel,
+                       prec == CHEM_MIXED ? h->opts.conv_kappa_mixed : h->opts.conv_kappa,
+                       prec == CHEM_MIXED ? h->opts.max_newton_mixed : h->opts.max_newton,
+                       h->opts.max_halvings, h->opts.max_attempts, h->opts.point_implicit,
+                       h->opts.div_check};
+}
+
 int launch_cfg(Handle *h, const chem_advance_args *a, int prec, const LaunchCfg *cfg,
                unsigned long long *counter) {
     cudaStream_t st = (cudaStream_t)a->stream;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "zeroing the work counter");
-    StepOptions o{h->opts.rtol, h->opts.atol_rel,
-                  prec == CHEM_MIXED ? h->opts.conv_kappa_mixed : h->opts.conv_kappa,
-                  prec == CHEM_MIXED ? h->opts.max_newton_mixed : h->opts.max_newton,
-                  h->opts.max_halvings, h->opts.max_attempts, h->opts.point_implicit,
-                  h->opts.div_check};
-    StepBatch b;
+    StepOptions o = step_options(h, prec);
+    StepBatch b{};
     b.n_cells = a->n_cells;
     b.ld = a->ld > 0 ? a->ld : a->n_cells;
     b.rho = a->rho_s;
@@ -868,6 +872,9 @@ int chem_create(const chem_mech_desc *mech, const chem_options *opts, chem_handl
         h->lanes[prec] = G;
         LaunchCfg *cfg;
         rc = get_cfg(h, prec, G, &cfg);
+        // (and the request server's queue instantiation, so that a server
+        // sets up this handle's lane without touching function attributes)
+        if (!rc) rc = get_cfg(h, prec, G, &cfg, true);
         if (rc) { chem_destroy(h); return rc; }
     }
     *out = h;

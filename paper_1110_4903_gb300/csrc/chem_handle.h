@@ -60,12 +60,14 @@ using Handle = ::chem_handle_s;
 
 int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
-int get_cfg(Handle *h, int prec, int G, LaunchCfg **out);
-int configure(Handle *h, int prec, int G, int wpb, LaunchCfg &cfg);
+int get_cfg(Handle *h, int prec, int G, LaunchCfg **out, bool queue = false);
+int configure(Handle *h, int prec, int G, int wpb, LaunchCfg &cfg, bool queue = false);
+const void *be_kernel_queue(int prec, int G);
 int launch_step(Handle *h, const chem_advance_args *a, int prec, int G, unsigned long long *counter);
 int launch_cfg(Handle *h, const chem_advance_args *a, int prec, const LaunchCfg *cfg,
                unsigned long long *counter);
 unsigned long long *next_counter(Handle *h);
+StepOptions step_options(const Handle *h, int prec);
 void fill_log_table(std::vector<double> &tab);
 void destroy_serving(Handle *h);
 }  // namespace chem

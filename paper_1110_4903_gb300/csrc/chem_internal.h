@@ -146,6 +146,46 @@ struct StepOptions {
     int max_newton, max_halvings, max_attempts, point_implicit, div_check;
 };
 
+// Device work queue of the request server: requests published in a ring of
+// descriptors in host memory mapped into the device's address space, their
+// cells numbered consecutively ("virtual cells") in publication order.  (The
+// server publishes requests in chunks, one descriptor each, interleaved
+// across requests; to the kernel a chunk is a request.)  A
+// free slot of a running step kernel claims the next published virtual cell
+// (a compare-and-swap on `next` below `tail`), finds its request by scanning
+// the ring from `oldest`, steps the cell and counts it done; the slot that
+// completes a request's last cell publishes its completion record.
+struct ServeDesc {              // host-written, one per ring entry
+    long long seq;              // request sequence number held by the entry
+    long long start, n_cells;   // its first virtual cell and cell count
+    long long ld;               // leading dimension of rho
+    double *rho, *e, *T_out;    // device state and optional output
+    int *status;                // optional per-cell status
+    double dt;
+    long long pad;
+};
+struct ServeDone {              // kernel-written, one per ring entry
+    long long seq;              // written last: the request with this seq is done
+    unsigned long long t_first; // globaltimer (ns) of its first cell's claim
+    unsigned long long t_last;  // and of its last cell's completion
+    long long pad;
+};
+struct ServeQueue {
+    const ServeDesc *desc;              // [cap], mapped host memory
+    ServeDone *fin;                     // [cap], mapped host memory
+    const unsigned long long *tail;     // mapped host: published virtual cells
+    unsigned long long *front;          // mapped host: a recent claim (every 32nd), for the host's window
+    const long long *oldest;            // mapped host: lowest unfinished seq
+    const int *budget;                  // mapped host: this launch's blocks >= budget claim nothing
+    unsigned long long *next;           // device: claimed virtual cells
+    unsigned long long *done;           // device [cap]: cells done per entry
+    unsigned long long *t_first;        // device [cap]
+    unsigned long long *t_last;         // device [cap]
+    int cap;
+    long long linger_ns;                // a warp with no work waits this long for more, then exits
+    int *error;                         // device: set when a scan or wait runs past its bound
+};
+
 struct StepBatch {
     long long n_cells, ld;
     double *rho;
@@ -165,6 +205,9 @@ struct StepBatch {
     // optional record of the state after each of a cell's first kSubstepStates
     // accepted substeps: [cell][substep][ns + 1]
     double *substep_states;
+    // request-server mode (the kernel's queue instantiation): cells come from
+    // this queue instead of [0, n_cells) of the buffers above
+    ServeQueue queue;
 };
 
 // Words of the per-cell substep-schedule record (256 attempts).

@@ -1049,10 +1049,85 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     T_pred = T + des * dTde;
 }
 
+// ---- request-server queue (ServeQueue in chem_internal.h) -----------------
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T ld_vol(const T *p) {
+    return *reinterpret_cast<const volatile T *>(p);
+}
+// Claims the next published virtual cell for this block, or returns -1 when
+// none is published or the launch's block budget excludes this block.  The
+// compare-and-swap loop ends: each failure means another slot advanced
+// `next`, and it only advances below `tail`.
+__device__ __forceinline__ long long serve_claim(const ServeQueue &q) {
+    if ((int)blockIdx.x >= ld_vol(q.budget)) return -1;
+    const unsigned long long tail = ld_acquire_sys(q.tail);
+    unsigned long long cur = ld_vol(q.next);
+    while (cur < tail) {
+        const unsigned long long prev = atomicCAS(q.next, cur, cur + 1);
+        if (prev == cur) {
+            if ((cur & 31) == 0) *reinterpret_cast<volatile unsigned long long *>(q.front) = cur;
+            return (long long)cur;
+        }
+        cur = prev;
+    }
+    return -1;
+}
+// The ring entry of the request holding virtual cell v (and the cell's index
+// in it): the request is unfinished, so its sequence number is in
+// [oldest, oldest + cap).  -1, with the error flag set, if it is not found.
+__device__ __forceinline__ int serve_find(const ServeQueue &q, long long v, long long &cell) {
+    long long s = ld_vol(q.oldest);
+#pragma unroll 1
+    for (int guard = 0; guard < q.cap; ++guard, ++s) {
+        const ServeDesc *d = q.desc + (s % q.cap);
+        if (ld_vol(&d->seq) != s) continue;
+        const long long st = ld_vol(&d->start), nc = ld_vol(&d->n_cells);
+        if (v >= st && v < st + nc) {
+            cell = v - st;
+            return (int)(s % q.cap);
+        }
+    }
+    atomicExch(q.error, 1);
+    return -1;
+}
+// Counts a finished cell of ring entry e (lane 0 of its slot); the slot that
+// finishes the request's last cell resets the entry's counters for the next
+// request and publishes the completion record to the host.
+__device__ __forceinline__ void serve_cell_done(const ServeQueue &q, int e) {
+    __threadfence();   // the cell's results before its count
+    atomicMax(q.t_last + e, globaltimer_ns());
+    __threadfence();
+    const unsigned long long prev = atomicAdd(q.done + e, 1ULL);
+    const ServeDesc *d = q.desc + e;
+    if ((long long)prev + 1 == ld_vol(&d->n_cells)) {
+        const unsigned long long tf = atomicExch(q.t_first + e, ~0ULL);
+        const unsigned long long tl = atomicExch(q.t_last + e, 0ULL);
+        atomicExch(q.done + e, 0ULL);
+        __threadfence_system();
+        volatile ServeDone *f = q.fin + e;
+        f->t_first = tf;
+        f->t_last = tl;
+        __threadfence_system();
+        f->seq = ld_vol(&d->seq);
+    }
+}
+
 // At most 10 warps per block and 102 registers per thread: 20 warps fit on
 // an SM when shared memory allows it (2 blocks of 10; the mixed path at 36
 // species, 11.3 KB per cell).
-template <int G, typename JT>
+// Q: request-server mode, cells claimed from b.queue (each slot's request
+// descriptor in host memory; its dt, buffers and completion accounting).
+template <int G, typename JT, bool Q = false>
 __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, StepOptions o, StepBatch b) {
     extern __shared__ __align__(16) char smem[];
     constexpr int S = 32 / G;
@@ -1069,20 +1144,38 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
 
     int state = kFree;
     long long cell = -1;
+    // request-server mode: the slot's ring entry and its request's dt
+    int qe = -1;
+    double sdt = b.dt;
+    unsigned long long idle_since = 0;
     double T = 1500.0, T0 = 1500.0, Tin = CUDART_NAN, h = 0.0, norm_prev = CUDART_INF;
     double atol_rho = 0.0, atol_e = 0.0;
     int k = 0, level = 0, attempts = 0, iters = 0, subs = 0, fails = 0;
     long long t_units = 0;
     const long long total = 1LL << o.max_halvings;
 
-    auto write_fail = [&](int code) {
+    // per-cell outputs (lane 0 of the slot); in request-server mode the
+    // request's own buffers, and the cell counted done
+    auto emit = [&](int code, double Tv) {
         if (sl == 0) {
-            if (b.status) b.status[cell] = code;
-            if (b.T_out) b.T_out[cell] = Tin;
-            if (b.newton_iters) b.newton_iters[cell] = iters;
-            if (b.substeps) b.substeps[cell] = subs;
-            if (b.failures) b.failures[cell] = fails;
+            if constexpr (Q) {
+                const ServeDesc *d = b.queue.desc + qe;
+                int *st = ld_vol(&d->status);
+                double *to = ld_vol(&d->T_out);
+                if (st) st[cell] = code;
+                if (to) to[cell] = Tv;
+                serve_cell_done(b.queue, qe);
+            } else {
+                if (b.status) b.status[cell] = code;
+                if (b.T_out) b.T_out[cell] = Tv;
+                if (b.newton_iters) b.newton_iters[cell] = iters;
+                if (b.substeps) b.substeps[cell] = subs;
+                if (b.failures) b.failures[cell] = fails;
+            }
         }
+    };
+    auto write_fail = [&](int code) {
+        emit(code, Tin);
         state = kFree;
     };
     auto start_substep = [&]() {
@@ -1091,7 +1184,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
             return;
         }
         while ((total >> level) > total - t_units) ++level;
-        h = ldexp(b.dt, -level);
+        h = ldexp(sdt, -level);
         ++attempts;
 #pragma unroll 1
         for (int i = sl; i < n; i += G) sm.x[i] = sm.x0[i];
@@ -1115,23 +1208,49 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             long long got = -1;
-            if (state == kFree && sl == 0) got = (long long)atomicAdd(b.work_counter, 1ULL);
-            got = __shfl_sync(kFull, got, slot * G);
-            const bool loading = state == kFree && got < b.n_cells;
-            if (state == kFree && !loading) state = kDead;
+            bool loading;
+            const double *rho_in = b.rho, *e_in = b.e;
+            long long ld_in = b.ld;
+            if constexpr (Q) {
+                // claim the next published cell, find its request
+                int e = -1;
+                if (state == kFree && sl == 0) {
+                    got = serve_claim(b.queue);
+                    if (got >= 0) {
+                        e = serve_find(b.queue, got, cell);
+                        if (e >= 0) atomicMin(b.queue.t_first + e, globaltimer_ns());
+                    }
+                }
+                e = __shfl_sync(kFull, e, slot * G);
+                cell = __shfl_sync(kFull, cell, slot * G);
+                loading = state == kFree && e >= 0;
+                if (loading) {
+                    qe = e;
+                    const ServeDesc *d = b.queue.desc + qe;
+                    rho_in = ld_vol(&d->rho);
+                    e_in = ld_vol(&d->e);
+                    ld_in = ld_vol(&d->ld);
+                    sdt = ld_vol(&d->dt);
+                }
+            } else {
+                if (state == kFree && sl == 0) got = (long long)atomicAdd(b.work_counter, 1ULL);
+                got = __shfl_sync(kFull, got, slot * G);
+                loading = state == kFree && got < b.n_cells;
+                if (state == kFree && !loading) state = kDead;
+                if (loading) cell = got;
+            }
             int nonfin = 0;
             double rt = 0.0, es = 0.0;
             if (loading) {
-                cell = got;
                 iters = subs = fails = 0;
                 Tin = CUDART_NAN;
-                if (b.schedule && sl == 0) {
+                if (!Q && b.schedule && sl == 0) {
 #pragma unroll 1
                     for (int w = 0; w < kSchedWords; ++w) b.schedule[cell * kSchedWords + w] = 0u;
                 }
 #pragma unroll 1
                 for (int i = sl; i < n; i += G) {
-                    const double v = i < ns ? b.rho[(size_t)i * b.ld + cell] : b.e[cell];
+                    const double v = i < ns ? rho_in[(size_t)i * ld_in + cell] : e_in[cell];
                     sm.x0[i] = v;
                     sm.x[i] = v;
                     if (!isfinite(v)) nonfin = 1;
@@ -1149,7 +1268,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
             if (loading) {
                 atol_rho = o.atol_rel * rt;
                 atol_e = o.atol_rel * es;
-                T = b.T_in ? b.T_in[cell] : 1500.0;
+                T = (!Q && b.T_in) ? b.T_in[cell] : 1500.0;
                 if (nonfin || !(rt > 0.0))
                     write_fail(kCellBadInput);
                 else
@@ -1172,14 +1291,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
                     write_fail(kCellTFailed);
                 } else {
                     T = T0 = Tin = Tr;
-                    if (b.dt == 0.0) {
-                        if (sl == 0) {
-                            if (b.status) b.status[cell] = kCellOk;
-                            if (b.T_out) b.T_out[cell] = Tr;
-                            if (b.newton_iters) b.newton_iters[cell] = 0;
-                            if (b.substeps) b.substeps[cell] = 0;
-                            if (b.failures) b.failures[cell] = 0;
-                        }
+                    if (sdt == 0.0) {
+                        emit(kCellOk, Tr);
                         state = kFree;
                     } else {
                         t_units = 0;
@@ -1202,11 +1315,11 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
                     T = Tr;
                     // accept the substep (and record it: attempt attempts - 1
                     // < 32 kSchedWords, the budget being capped when recording)
-                    if (b.schedule && sl == 0) {
+                    if (!Q && b.schedule && sl == 0) {
                         const int a = attempts - 1;
                         b.schedule[cell * kSchedWords + (a >> 5)] |= 1u << (a & 31);
                     }
-                    if (b.substep_states && subs < kSubstepStates) {
+                    if (!Q && b.substep_states && subs < kSubstepStates) {
                         double *rec = b.substep_states + ((size_t)cell * kSubstepStates + subs) * n;
 #pragma unroll 1
                         for (int i = sl; i < n; i += G) rec[i] = sm.x[i];
@@ -1218,20 +1331,27 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
                     ++subs;
                     if (level > 0) --level;
                     if (t_units == total) {
+                        double *rho_out = b.rho, *e_out = b.e;
+                        long long ld_out = b.ld;
+                        if constexpr (Q) {
+                            const ServeDesc *d = b.queue.desc + qe;
+                            rho_out = ld_vol(&d->rho);
+                            e_out = ld_vol(&d->e);
+                            ld_out = ld_vol(&d->ld);
+                        }
 #pragma unroll 1
                         for (int i = sl; i < n; i += G) {
                             if (i < ns)
-                                b.rho[(size_t)i * b.ld + cell] = sm.x[i];
+                                rho_out[(size_t)i * ld_out + cell] = sm.x[i];
                             else
-                                b.e[cell] = sm.x[i];
+                                e_out[cell] = sm.x[i];
                         }
-                        if (sl == 0) {
-                            if (b.status) b.status[cell] = kCellOk;
-                            if (b.T_out) b.T_out[cell] = T;
-                            if (b.newton_iters) b.newton_iters[cell] = iters;
-                            if (b.substeps) b.substeps[cell] = subs;
-                            if (b.failures) b.failures[cell] = fails;
+                        if constexpr (Q) {
+                            // every lane's results before lane 0 counts the cell done
+                            // (the slot's G lanes are converged here)
+                            __syncwarp(G == 32 ? kFull : (((1u << G) - 1u) << (slot * G)));
                         }
+                        emit(kCellOk, T);
                         state = kFree;
                     } else {
                         start_substep();
@@ -1242,8 +1362,22 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
         }
         if (!__any_sync(kFull, state == kNewtonReady)) {
             if (__all_sync(kFull, state == kDead)) break;
+            if constexpr (Q) {
+                // no published cell for any slot of the warp: poll for more
+                // (bounded by the linger time, then the warp leaves)
+                if (__all_sync(kFull, state == kFree)) {
+                    const unsigned long long now = globaltimer_ns();
+                    if (idle_since == 0) idle_since = now;
+                    // one decision for the whole warp
+                    if (__any_sync(kFull, (int)blockIdx.x >= ld_vol(b.queue.budget) ||
+                                              now - idle_since > (unsigned long long)b.queue.linger_ns))
+                        break;
+                    __nanosleep(20000);
+                }
+            }
             continue;
         }
+        if constexpr (Q) idle_since = 0;
         // one Newton iteration of Eq. 29 for every slot
         double norm = 0.0, T_pred = T;
         bool bad = false;

@@ -63,14 +63,15 @@ def test_alone_equals_mixed(env):
         r, ev = rho.clone(), e.clone()
         tickets.append(srv.submit(mechs[ns][1], r, ev, dt))
         mixed.append((r, ev))
-    starts = []
+    spans = []
     for t in tickets:
         res = srv.wait(t)
         assert res.state == chem.REQ_DONE
-        starts.append((res.t_start, res.t_done))
-    # several requests were on the device at the same time
-    overlap = sum(1 for i in range(len(starts)) for j in range(i)
-                  if starts[i][0] < starts[j][1] and starts[j][0] < starts[i][1])
+        assert 0 < res.dev_first_ns <= res.dev_last_ns
+        spans.append((res.dev_first_ns, res.dev_last_ns))
+    # several requests had cells on the device at the same time (device clock)
+    overlap = sum(1 for i in range(len(spans)) for j in range(i)
+                  if spans[i][0] < spans[j][1] and spans[j][0] < spans[i][1])
     assert overlap > 0
     for (ra, ea), (rm, em) in zip(alone, mixed):
         assert torch.equal(ra, rm) and torch.equal(ea, em)
@@ -82,6 +83,79 @@ def test_alone_equals_mixed(env):
     assert torch.equal(r, mixed[1][0])
     st = srv.stats()
     assert st["failed"] == 0 and st["completed"] == 2 * len(reqs) and st["bytes_in_use"] == 0
+    srv.close()
+
+
+def test_small_requests_join_a_running_grid(env):
+    """Continuous batching on the device: small requests submitted while a
+    large one of the same mechanism runs are claimed by slots that free up
+    inside the running grid -- their first cell starts and their last cell
+    finishes before the large request's last cell (device clock) -- and each
+    result equals chem_advance_ex's on the same input."""
+    torch, chem, mechs = env
+    m, h = mechs[36]
+    big = _states(torch, m, 1 << 17, seed=11)
+    smalls = [_states(torch, m, n, seed=200 + i) for i, n in enumerate([512, 800, 1000, 1500, 700, 2000, 900, 1200])]
+    refs = []
+    for r, e in smalls:
+        rr, ee = r.clone(), e.clone()
+        h.advance(rr, ee, 1e-6)
+        refs.append((rr, ee))
+    torch.cuda.synchronize()
+    srv = chem.Server()
+    launches0 = srv.stats()["launches"]
+    rb, eb = big[0].clone(), big[1].clone()
+    tb = srv.submit(h, rb, eb, 1e-6)
+    import time
+    time.sleep(0.03)                       # the large request is running
+    assert srv.poll(tb).state == chem.REQ_RUNNING
+    work = [(r.clone(), e.clone()) for r, e in smalls]
+    ts = [srv.submit(h, r, e, 1e-6) for r, e in work]
+    res_b = srv.wait(tb)
+    assert res_b.state == chem.REQ_DONE
+    inside = 0
+    for t, (r, e), (rr, ee) in zip(ts, work, refs):
+        res = srv.wait(t)
+        assert res.state == chem.REQ_DONE
+        assert torch.equal(r, rr) and torch.equal(e, ee)
+        assert res.dev_first_ns > res_b.dev_first_ns
+        inside += res.dev_last_ns < res_b.dev_last_ns
+    assert inside == len(ts), inside
+    st = srv.stats()
+    # one lane, one kernel instance carried the large and the small requests
+    assert st["launches"] - launches0 == 1 and st["queue_errors"] == 0
+    srv.close()
+
+
+def test_two_mechanisms_share_the_device(env):
+    """Small requests of a second mechanism get a share of the GPU while a
+    large request of the first runs: they finish before it does."""
+    torch, chem, mechs = env
+    m36, h36 = mechs[36]
+    m9, h9 = mechs[9]
+    big = _states(torch, m36, 1 << 17, seed=12)
+    smalls = [_states(torch, m9, n, seed=300 + i) for i, n in enumerate([4000, 9000, 6000, 12000])]
+    # (references first: a plain launch cannot start while the server's
+    # persistent kernel holds the SMs)
+    refs = []
+    for r, e in smalls:
+        rr, ee = r.clone(), e.clone()
+        h9.advance(rr, ee, 1e-6)
+        refs.append((rr, ee))
+    torch.cuda.synchronize()
+    srv = chem.Server()
+    tb = srv.submit(h36, big[0], big[1], 1e-6)
+    import time
+    time.sleep(0.03)
+    assert srv.poll(tb).state == chem.REQ_RUNNING
+    ts = [srv.submit(h9, r, e, 1e-6) for r, e in smalls]
+    res_b = srv.wait(tb)
+    for t, (r, e), (rr, ee) in zip(ts, smalls, refs):
+        res = srv.wait(t)
+        assert res.state == chem.REQ_DONE
+        assert res.dev_last_ns < res_b.dev_last_ns
+        assert torch.equal(r, rr) and torch.equal(e, ee)
+    assert srv.stats()["queue_errors"] == 0
     srv.close()
 
 
