@@ -18,6 +18,33 @@ import sys
 import numpy as np
 
 
+def initial_field(mech, cells):
+    """A hot kernel (2400 K, with a small pool of H, O and OH radicals) in
+    cold H2-air reactants at 1 atm: (T [cells], P [cells], Y [ns, cells])."""
+    x = np.arange(cells) / cells
+    g = np.exp(-((x - 0.5) / 0.05) ** 2)
+    T = 400.0 + 2000.0 * g
+    Y = np.zeros((mech.ns, cells))
+    names = mech.species
+    rad = {"H": 2e-4, "O": 1e-3, "OH": 2e-3}
+    for sp, y in rad.items():
+        Y[names.index(sp)] = y * g
+    rest = 1.0 - Y.sum(0)
+    Y[names.index("H2")] = 0.028 * rest
+    Y[names.index("O2")] = 0.226 * rest
+    Y[names.index("N2")] = 0.746 * rest
+    return T, np.full(cells, 101325.0), Y
+
+
+def advect(rho, e, c, roll):
+    """The convection half: first-order upwind advection of the conserved
+    densities at Courant number c on a periodic domain, in place, for torch
+    tensors or numpy arrays (`roll(a, shift, axis)`): a <- a - c (a - a[i-1]),
+    each element by the same IEEE operations on either."""
+    rho -= c * (rho - roll(rho, 1, 1))
+    e -= c * (e - roll(e, 1, 0))
+
+
 def run(cells=4096, steps=20, cfl=0.5, dx=50e-6, u=500.0, precision=1, use_graph=True):
     import torch
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -26,19 +53,12 @@ def run(cells=4096, steps=20, cfl=0.5, dx=50e-6, u=500.0, precision=1, use_graph
     mech = synth.h2_air_9sp()
     ch = chem.Chem(mech, precision=precision)
     dev = torch.device("cuda")
-    # a hot kernel of burnt gas in cold reactants
-    x = np.arange(cells) / cells
-    T = 400.0 + 2000.0 * np.exp(-((x - 0.5) / 0.05) ** 2)
-    Y = np.zeros((mech.ns, cells))
-    names = mech.species
-    Y[names.index("H2")] = 0.028
-    Y[names.index("O2")] = 0.226
-    Y[names.index("N2")] = 0.746
+    T, P, Y = initial_field(mech, cells)
     Tt = torch.tensor(T, device=dev)
     rho = torch.empty((mech.ns, cells), dtype=torch.float64, device=dev)
     e = torch.empty(cells, dtype=torch.float64, device=dev)
-    ch.state_from_tpy(Tt, torch.full((cells,), 101325.0, dtype=torch.float64, device=dev),
-                      torch.tensor(Y, device=dev), rho, e)
+    ch.state_from_tpy(Tt, torch.tensor(P, device=dev), torch.tensor(Y, device=dev), rho, e)
+    rho0, e0 = rho.clone(), e.clone()
     dt = cfl * dx / u
     ef = torch.tensor(ch.formation_energies(), device=dev)
     status = torch.zeros(cells, dtype=torch.int32, device=dev)
@@ -48,10 +68,13 @@ def run(cells=4096, steps=20, cfl=0.5, dx=50e-6, u=500.0, precision=1, use_graph
     U0 = (e.sum() + (ef[:, None] * rho).sum()).item()
     c = u * dt / dx
     hist = []
+
+    def troll(a, shift, axis):
+        return torch.roll(a, shift, dims=axis if a.dim() > 1 else 0)
+
     for n in range(steps):
         # convection half: upwind, conservative, periodic
-        rho -= c * (rho - torch.roll(rho, 1, dims=1))
-        e -= c * (e - torch.roll(e, 1))
+        advect(rho, e, c, troll)
         # chemistry half
         if g is not None:
             g.launch()
@@ -65,8 +88,10 @@ def run(cells=4096, steps=20, cfl=0.5, dx=50e-6, u=500.0, precision=1, use_graph
         g.close()
     ch.close()
     scale = float(e.abs().sum() + (ef.abs()[:, None] * rho.abs()).sum())
-    return {"cells": cells, "steps": steps, "dt": dt, "mass_drift": abs(hist[-1]["mass"] - m0) / m0,
-            "energy_drift": abs(hist[-1]["U"] - U0) / scale, "history": hist}
+    return {"cells": cells, "steps": steps, "dt": dt, "c": c, "mass_drift": abs(hist[-1]["mass"] - m0) / m0,
+            "energy_drift": abs(hist[-1]["U"] - U0) / scale, "history": hist,
+            "rho0": rho0.cpu().numpy(), "e0": e0.cpu().numpy(), "rho": rho.cpu().numpy(),
+            "e": e.cpu().numpy(), "T": T_out.cpu().numpy()}
 
 
 def main():
@@ -75,7 +100,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     args = ap.parse_args()
     out = run(args.cells, args.steps)
-    print(json.dumps({k: v for k, v in out.items() if k != "history"}))
+    print(json.dumps({k: v for k, v in out.items() if k in ("cells", "steps", "dt", "mass_drift", "energy_drift")}))
     for h in out["history"]:
         print(json.dumps(h))
 
