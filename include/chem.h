@@ -168,7 +168,10 @@ typedef struct chem_advance_args {
 /* Accepted substeps whose states chem_advance_args.substep_states records. */
 #define CHEM_SUBSTEP_STATES 32
 
-/* chem_advance with strides, temperature guesses and per-cell outputs. */
+/* chem_advance with strides, temperature guesses and per-cell outputs.
+ * Each launch takes one of the handle's 4096 work counters in turn (zeroed
+ * in-stream before it): at most 4096 launches of one handle may be in flight
+ * at once, across all the streams it is used on. */
 int chem_advance_ex(chem_handle_t h, const chem_advance_args *a);
 
 /* Domain-segmented execution (Sec. 5.2): the same step as chem_advance_ex,
@@ -189,7 +192,8 @@ int chem_advance_host(chem_handle_t h, int64_t n_cells, int64_t ld, double *rho_
  * callers that must not allocate device memory while running (a host flow
  * solver inside a framework that owns the device through its own memory
  * pool, or a real-time loop that forbids cudaMalloc/cudaFree after start-up).
- * Same arguments and results as chem_advance_host, but the device staging of
+ * Same arguments as chem_advance_host, and the same results for the same
+ * launch shape, but the device staging of
  * rho_s, e, T_out, status and the kernel's work counter lives in one fixed
  * 16 MiB file-scope device array (chem_static_scratch_bytes reports the
  * size) that every GPU loading the library keeps until exit; nothing is
@@ -200,6 +204,10 @@ int chem_advance_host(chem_handle_t h, int64_t n_cells, int64_t ld, double *rho_
  * must be current).  All calls share the array and it keeps the last call's
  * contents; calls are serialised per device inside one process, and calls
  * that overlapped on the GPU would race.  Synchronous. */
+/* (It never autotunes -- the tuner's sample buffers are allocations: it
+ * launches the lane width the handle holds for its precision.  With
+ * chem_options.autotune set, call chem_autotune once beforehand to get the
+ * tuned shape.) */
 int chem_advance_host_static(chem_handle_t h, int64_t n_cells, int64_t ld, double *rho_s,
                              double *e, double dt, double *T_out, int32_t *status);
 

@@ -22,7 +22,9 @@ struct LaunchCfg {
 };
 
 // Work counters: one per launch, taken round-robin, zeroed in-stream before
-// the launch that uses it.
+// the launch that uses it.  A counter is reused after kCounterRing further
+// launches of the handle, so at most that many of its launches may be in
+// flight at once (on whatever streams); chem.h states the limit.
 constexpr unsigned kCounterRing = 4096;
 
 struct ServingState;
