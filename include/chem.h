@@ -353,26 +353,39 @@ int chem_server_stats(chem_server_t s, chem_server_stats_t *out);
 
 /* ---- batched dense solves: the kinetics-only experiment of Sec. 5.2 ----
  * Solves n_sys independent systems A_k x_k = b_k of size n (1..CHEM_LU_MAX_N)
- * in place by Gaussian elimination with row partial pivoting (ties to the
- * lowest row) in FP64; every arithmetic step of the factorisation is
- * explicitly rounded and in the scalar order (multiplier a_ij / a_jj, update
- * a_ik - l a_jk without contraction), so the factors and pivots equal a
- * scalar elimination bit for bit; x equals the row-by-row substitutions bit
- * for bit (CHEM_LU_GLOBAL) or to rounding (CHEM_LU_ONCHIP, which runs the
- * back substitution by columns across the warp).  On return A holds L (unit, below the
- * diagonal) and U, b holds x, pivots[k*n + j] (optional) the row swapped
- * into row j, info[k] (optional) 0 or 1 + the first column with a zero or
- * non-finite pivot.  Layout and kernel by method:
- *   CHEM_LU_GLOBAL  A[(i*n + j)*n_sys + k], b[i*n_sys + k] (interleaved);
- *                   one thread per system, the matrices stay in HBM (the
- *                   paper's global-memory approach).
- *   CHEM_LU_ONCHIP  A[(k*n + i)*n + j], b[k*n + i] (contiguous); one warp
- *                   per system, the matrix in shared memory
- *                   (CHEM_E_UNSUPPORTED when n*(n+1) doubles do not fit).
- * Device pointers; asynchronous on `stream`. */
-#define CHEM_LU_GLOBAL 0
-#define CHEM_LU_ONCHIP 1
-#define CHEM_LU_MAX_N  256
+ * in place by Gaussian elimination with row partial pivoting in FP64: the
+ * pivot of column j is the first row i >= j of largest |a_ij| (a NaN
+ * diagonal stays the pivot; a NaN below it is never taken).  On return A
+ * holds L (unit, below the diagonal) and U, b holds x, pivots[k*n + j]
+ * (optional) the row swapped into row j, info[k] (optional) 0 or 1 + the
+ * first column with a zero or non-finite pivot (elimination continues past
+ * it; that system's A and x are then meaningless).  Arithmetic, layout and
+ * kernel by method:
+ *   CHEM_LU_GLOBAL      A[(i*n + j)*n_sys + k], b[i*n_sys + k] (interleaved);
+ *                       the matrices stay in HBM (the paper's global-memory
+ *                       approach): a thread per system when the systems
+ *                       fill the GPU, else a block of warps per 32 systems
+ *                       sharing each step's rows.  Every step explicitly
+ *                       rounded in the scalar order (multiplier a_ij / a_jj,
+ *                       update a_ik - l a_jk without contraction): factors,
+ *                       pivots and x equal a scalar elimination with
+ *                       row-by-row substitutions bit for bit.
+ *   CHEM_LU_GLOBAL_FMA  same layout and kernels, contracted arithmetic:
+ *                       multipliers a_ij times one reciprocal of the pivot,
+ *                       updates and substitutions as fused multiply-adds;
+ *                       equal to the scalar elimination to rounding.
+ *   CHEM_LU_ONCHIP      A[(k*n + i)*n + j], b[k*n + i] (contiguous); one warp
+ *                       per system, the matrix in shared memory
+ *                       (CHEM_E_UNSUPPORTED when n*(n+1) doubles do not
+ *                       fit); factors and pivots bit for bit as
+ *                       CHEM_LU_GLOBAL, x to rounding (the back
+ *                       substitution runs by columns across the warp).
+ * Device pointers; asynchronous on `stream`; CHEM_E_INVALID_ARG for an
+ * unknown method, n out of range, n_sys < 0 or a null A or b. */
+#define CHEM_LU_GLOBAL     0
+#define CHEM_LU_ONCHIP     1
+#define CHEM_LU_GLOBAL_FMA 2
+#define CHEM_LU_MAX_N      256
 int chem_batched_solve(int32_t method, int32_t n, int64_t n_sys, double *A, double *b,
                        int32_t *pivots, int32_t *info, void *stream);
 

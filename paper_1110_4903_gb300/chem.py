@@ -82,7 +82,7 @@ class ServerStats(C.Structure):
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
-LU_GLOBAL, LU_ONCHIP = 0, 1
+LU_GLOBAL, LU_ONCHIP, LU_GLOBAL_FMA = 0, 1, 2
 
 _lib = None
 
@@ -400,8 +400,9 @@ class Server:
 
 def batched_solve(method, A, b, pivots=None, info=None, stream=None):
     """In-place batched solve of device tensors (chem_batched_solve):
-    LU_GLOBAL: A [n, n, n_sys], b [n, n_sys]; LU_ONCHIP: A [n_sys, n, n], b [n_sys, n]."""
-    if method == LU_GLOBAL:
+    LU_GLOBAL and LU_GLOBAL_FMA: A [n, n, n_sys], b [n, n_sys]; LU_ONCHIP:
+    A [n_sys, n, n], b [n_sys, n]."""
+    if method in (LU_GLOBAL, LU_GLOBAL_FMA):
         n, n_sys = int(A.shape[0]), int(A.shape[2])
     else:
         n_sys, n = int(A.shape[0]), int(A.shape[1])

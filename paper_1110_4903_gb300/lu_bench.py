@@ -1,7 +1,11 @@
 """Batched dense solves on the GPU: the kinetics-only experiment of Sec. 5.2
-(Gaussian elimination over many independent N_s x N_s systems), global-memory
-kernel (one thread per system, matrices in HBM) against the on-chip kernel
-(one warp per system, matrix in shared memory).  One JSON line per case.
+(Gaussian elimination over many independent N_s x N_s systems).  The
+global-memory kernels (matrices in HBM; a thread per system, or a block of
+warps per 32 systems when there are few), in the scalar rounding order and
+contracted (FMA), against the on-chip kernel (one warp per system, matrix in
+shared memory).  One JSON line per case, with the fraction of the measured
+HBM bandwidth (by the paper's byte count of the elimination) and of the FP64
+pipe (by the operation count, divisions as one).
 
   python -m paper_1110_4903_gb300.lu_bench [--sizes 10,37,100,200] [--bytes 2e9]
 """
@@ -16,10 +20,15 @@ import numpy as np
 
 HBM_PEAK_GBS = 6677.8          # measured copy bandwidth of this GB300 pool
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 pipe: two lane-operations per clock per SM (a warp instruction every
+# 16 cycles), whatever the instruction (FMA, multiply or add)
+FP64_PIPE_TOPS = 152 * 2 * 2.07e9 / 1e12
 
 
 def flops(n):
-    """FP64 operations of one factorisation and one solve (divide = 1)."""
+    """FP64 operations of one factorisation and one solve (divide = 1).
+    Without FMA contraction each is one FP64 pipe instruction, except the
+    divisions (n (n + 1) / 2 of them), which take several."""
     lu = sum((n - j - 1) + 2 * (n - j - 1) * (n - j - 1) for j in range(n))
     return lu + 2 * n * n
 
@@ -57,11 +66,13 @@ def main():
         n_sys = int(min(nbytes / (8 * n * n), 1 << 22))
         rng = np.random.default_rng(n)
         base = torch.tensor(rng.standard_normal((n, n)), device=dev)
-        for method, name in ((chem.LU_GLOBAL, "global"), (chem.LU_ONCHIP, "onchip")):
+        for method, name in ((chem.LU_GLOBAL, "global"), (chem.LU_GLOBAL_FMA, "global_fma"),
+                             (chem.LU_ONCHIP, "onchip")):
+            glob = method in (chem.LU_GLOBAL, chem.LU_GLOBAL_FMA)
             if method == chem.LU_ONCHIP and n * (n + 1) * 8 > 227 * 1024:
                 continue
             # diagonally shifted random systems, built on the device
-            if method == chem.LU_GLOBAL:
+            if glob:
                 A0 = (torch.randn((n, n, n_sys), dtype=torch.float64, device=dev) +
                       0.5 * n ** 0.5 * torch.eye(n, dtype=torch.float64, device=dev)[:, :, None])
                 b0 = torch.randn((n, n_sys), dtype=torch.float64, device=dev)
@@ -86,13 +97,14 @@ def main():
                     times.append(e0.elapsed_time(e1) * 1e-3)
             t = min(times)
             fl = flops(n) * n_sys
-            by = (global_bytes(n) if method == chem.LU_GLOBAL else 2 * 8 * (n * n + n)) * n_sys
+            by = (global_bytes(n) if glob else 2 * 8 * (n * n + n)) * n_sys
             line = {"case": "batched_solve", "method": name, "n": n, "systems": n_sys,
                     "seconds": t, "systems_per_s": n_sys / t, "gflops": fl / t / 1e9,
-                    "hbm_gbs": by / t / 1e9,
+                    "hbm_gbs": by / t / 1e9, "hbm_frac": by / t / 1e9 / HBM_PEAK_GBS,
+                    "fp64_pipe_frac": fl / t / 1e12 / FP64_PIPE_TOPS,
                     "roofline": ({"bound": "hbm", "achieved": by / t / 1e9, "peak": HBM_PEAK_GBS,
                                   "unit": "GB/s", "frac": by / t / 1e9 / HBM_PEAK_GBS}
-                                 if method == chem.LU_GLOBAL else
+                                 if glob else
                                  {"bound": "alu", "achieved": fl / t / 1e12, "peak": FP64_PEAK_TFLOPS,
                                   "unit": "TFLOP/s", "frac": fl / t / 1e12 / FP64_PEAK_TFLOPS}),
                     "singular": int((info != 0).sum().item())}

@@ -29,7 +29,7 @@ def _systems(n, n_sys, seed):
 
 
 @pytest.mark.parametrize("n,n_sys", [(1, 7), (10, 1000), (37, 333), (64, 100), (100, 40), (150, 9),
-                                     (200, 5)])
+                                     (200, 5), (10, 200000), (25, 80000)])
 @pytest.mark.parametrize("method", ["global", "onchip"])
 def test_bitwise_against_oracle(env, n, n_sys, method):
     torch, chem = env
@@ -64,6 +64,66 @@ def test_bitwise_against_oracle(env, n, n_sys, method):
             assert np.array_equal(x[k], xo)
         else:   # column-ordered back substitution: equal to rounding
             assert np.abs(x[k] - xo).max() <= 1e-13 * n * np.abs(xo).max()
+
+
+@pytest.mark.parametrize("n,n_sys", [(1, 7), (10, 1000), (37, 333), (100, 40), (200, 5), (10, 200000),
+                                     (25, 80000)])
+def test_contracted_against_oracle(env, n, n_sys):
+    """The contracted global elimination (reciprocal multipliers, FMA
+    updates): same pivots as the oracle, factors and x equal to rounding."""
+    torch, chem = env
+    A, b = _systems(n, n_sys, seed=n + 1)
+    dev = torch.device("cuda")
+    piv = torch.zeros((n_sys, n), dtype=torch.int32, device=dev)
+    info = torch.full((n_sys,), -1, dtype=torch.int32, device=dev)
+    Ad = torch.tensor(np.ascontiguousarray(A.transpose(1, 2, 0)), device=dev)
+    bd = torch.tensor(np.ascontiguousarray(b.T), device=dev)
+    chem.batched_solve(chem.LU_GLOBAL_FMA, Ad, bd, piv, info)
+    torch.cuda.synchronize()
+    LU = Ad.cpu().numpy().transpose(2, 0, 1)
+    x = bd.cpu().numpy().T
+    piv = piv.cpu().numpy()
+    assert (info.cpu().numpy() == 0).all()
+    eps = np.finfo(np.float64).eps
+    for k in range(0, n_sys, max(1, n_sys // 25)):
+        rc, LUo, pivo = oracle.lu_factor(A[k])
+        assert rc == 0 and np.array_equal(piv[k], pivo)
+        assert np.abs(LU[k] - LUo).max() <= 8 * n * eps * np.abs(LUo).max()
+        xo = oracle.lu_solve(LUo, pivo, b[k])
+        assert np.abs(x[k] - xo).max() <= 1e-13 * n * np.abs(xo).max()
+
+
+@pytest.mark.parametrize("n_sys", [5, 100000])
+@pytest.mark.parametrize("method", ["global", "global_fma"])
+def test_nan_and_singular_pivots_as_the_oracle(env, n_sys, method):
+    """Pivot choice around NaN and zero columns as in the oracle's search
+    (start from |a_jj|, take a row only if strictly larger): a NaN diagonal
+    stays the pivot and its column is singular; a NaN below the diagonal is
+    never the pivot; an all-zero column is singular.  Both global-memory
+    variants: a block of warps per 32 systems (few) and a thread per system
+    (many)."""
+    torch, chem = env
+    method = {"global": chem.LU_GLOBAL, "global_fma": chem.LU_GLOBAL_FMA}[method]
+    n = 4
+    A, b = _systems(n, n_sys, seed=3)
+    A[0, 0, 0] = np.nan
+    A[1, 2, 0] = np.nan
+    A[2, :, 1] = 0.0
+    dev = torch.device("cuda")
+    piv = torch.zeros((n_sys, n), dtype=torch.int32, device=dev)
+    info = torch.full((n_sys,), -1, dtype=torch.int32, device=dev)
+    Ad = torch.tensor(np.ascontiguousarray(A.transpose(1, 2, 0)), device=dev)
+    bd = torch.tensor(np.ascontiguousarray(b.T), device=dev)
+    chem.batched_solve(method, Ad, bd, piv, info)
+    torch.cuda.synchronize()
+    piv, info = piv.cpu().numpy(), info.cpu().numpy()
+    assert piv[0, 0] == 0 and info[0] == 1
+    rc, _, pivo = oracle.lu_factor(A[1])
+    assert pivo[0] != 2 and piv[1, 0] == pivo[0]
+    assert (rc != 0) == (info[1] != 0)
+    rc, _, pivo = oracle.lu_factor(A[2])
+    assert rc != 0 and piv[2, 0] == pivo[0] and info[2] == 2
+    assert (info[3:] == 0).all()
 
 
 def test_singular_and_unsupported(env):
