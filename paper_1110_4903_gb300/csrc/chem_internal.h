@@ -147,17 +147,31 @@ struct StepOptions {
 };
 
 // Device work queue of the request server: requests published in a ring of
-// descriptors in host memory mapped into the device's address space, their
-// cells numbered consecutively ("virtual cells") in publication order.  (The
-// server publishes requests in chunks, one descriptor each, interleaved
-// across requests; to the kernel a chunk is a request.)  A
-// free slot of a running step kernel claims the next published virtual cell
-// (a compare-and-swap on `next` below `tail`), finds its request by scanning
-// the ring from `oldest`, steps the cell and counts it done; the slot that
-// completes a request's last cell publishes its completion record.
+// descriptors in host memory mapped into the device's address space.  (The
+// server publishes requests in chunks of at most 2^kServeChunkLog cells, one
+// descriptor each, interleaved across requests; to the kernel a chunk is a
+// request.)  Chunk `seq` owns the virtual cells [seq, seq + 1) *
+// 2^kServeChunkLog, of which its first n_cells are real.  Chunks are handed
+// out in order: a warp's free slots take consecutive cells of the current
+// chunk together, by one atomic add on the chunk's claim counter (which
+// never fails, unlike a compare-and-swap on a shared position, whose
+// attempts collide at millions of claims per second); a claim past the
+// chunk's cells moves the current chunk on.  The slots step their cells and
+// count them done; the slot that completes a chunk's last cell resets the
+// entry's completion counters and publishes the chunk's completion record.
+//   Reads of mapped host memory cross the chip-to-chip link, and thousands of
+// warps issuing them stall one another, so the kernels keep device copies:
+// of `tail` and the launch's budget, refreshed by one warp at a time at most
+// every kServePollNs, and of each chunk's descriptor, copied into a device
+// ring by the first warp that claims from the chunk.
+constexpr long long kServePollNs = 2000;
+// A claim counter holds the ring lap of the chunk it counts (chunk / cap) in
+// its high bits, so a claim through a stale chunk number is recognised.
+constexpr int kClaimLapShift = 40;
+constexpr int kServeChunkLog = 10;
 struct ServeDesc {              // host-written, one per ring entry
-    long long seq;              // request sequence number held by the entry
-    long long start, n_cells;   // its first virtual cell and cell count
+    long long seq;              // chunk sequence number held by the entry
+    long long start, n_cells;   // its first virtual cell (seq << kServeChunkLog) and cell count
     long long ld;               // leading dimension of rho
     double *rho, *e, *T_out;    // device state and optional output
     int *status;                // optional per-cell status
@@ -173,17 +187,21 @@ struct ServeDone {              // kernel-written, one per ring entry
 struct ServeQueue {
     const ServeDesc *desc;              // [cap], mapped host memory
     ServeDone *fin;                     // [cap], mapped host memory
-    const unsigned long long *tail;     // mapped host: published virtual cells
-    unsigned long long *front;          // mapped host: a recent claim (every 32nd), for the host's window
-    const long long *oldest;            // mapped host: lowest unfinished seq
+    const unsigned long long *tail;     // mapped host: end of the last published chunk's real cells
+    unsigned long long *front;          // mapped host: a recent claim, for the host's window
     const int *budget;                  // mapped host: this launch's blocks >= budget claim nothing
-    unsigned long long *next;           // device: claimed virtual cells
+    ServeDesc *mdesc;                   // device [cap]: copies of the descriptors (seq -1: none)
+    unsigned long long *dtail;          // device: the latest `tail` read
+    int *dbudget;                       // device: the latest budget read (set before the launch)
+    unsigned long long *dpoll;          // device: globaltimer of the last read of the host values
+    unsigned long long *chunk;          // device: the chunk being handed out
+    unsigned long long *claimed;        // device [cap]: lap << kClaimLapShift | cells claimed
     unsigned long long *done;           // device [cap]: cells done per entry
     unsigned long long *t_first;        // device [cap]
     unsigned long long *t_last;         // device [cap]
     int cap;
     long long linger_ns;                // a warp with no work waits this long for more, then exits
-    int *error;                         // device: set when a scan or wait runs past its bound
+    int *error;                         // device: set when a claim finds a ring entry out of order
 };
 
 struct StepBatch {

@@ -1064,41 +1064,140 @@ template <typename T>
 __device__ __forceinline__ T ld_vol(const T *p) {
     return *reinterpret_cast<const volatile T *>(p);
 }
-// Claims the next published virtual cell for this block, or returns -1 when
-// none is published or the launch's block budget excludes this block.  The
-// compare-and-swap loop ends: each failure means another slot advanced
-// `next`, and it only advances below `tail`.
-__device__ __forceinline__ long long serve_claim(const ServeQueue &q) {
-    if ((int)blockIdx.x >= ld_vol(q.budget)) return -1;
-    const unsigned long long tail = ld_acquire_sys(q.tail);
-    unsigned long long cur = ld_vol(q.next);
-    while (cur < tail) {
-        const unsigned long long prev = atomicCAS(q.next, cur, cur + 1);
-        if (prev == cur) {
-            if ((cur & 31) == 0) *reinterpret_cast<volatile unsigned long long *>(q.front) = cur;
-            return (long long)cur;
-        }
-        cur = prev;
+// A relaxed load from L2 (not L1, which may hold another launch's or an
+// earlier chunk's copy): for device values that are either immutable while
+// they are read (a live chunk's descriptor copy) or only hints (`next`, the
+// budget copy, the poll time).  Unlike volatile loads, several of these can
+// be in flight at once.
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T *p) {
+    static_assert(sizeof(T) == 8 || sizeof(T) == 4, "8- or 4-byte values");
+    T r;
+    if constexpr (sizeof(T) == 8) {
+        const long long v = __ldcg(reinterpret_cast<const long long *>(p));
+        memcpy(&r, &v, 8);
+    } else {
+        const int v = __ldcg(reinterpret_cast<const int *>(p));
+        memcpy(&r, &v, 4);
     }
-    return -1;
+    return r;
 }
-// The ring entry of the request holding virtual cell v (and the cell's index
-// in it): the request is unfinished, so its sequence number is in
-// [oldest, oldest + cap).  -1, with the error flag set, if it is not found.
-__device__ __forceinline__ int serve_find(const ServeQueue &q, long long v, long long &cell) {
-    long long s = ld_vol(q.oldest);
+__device__ __forceinline__ long long ld_acquire_gpu(const long long *p) {
+    long long v;
+    asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+// Refreshes the device copies of the host's `tail` and of this launch's
+// budget: at most one warp per launch every kServePollNs reads host memory.
+__device__ __forceinline__ void serve_refresh(const ServeQueue &q) {
+    const unsigned long long now = globaltimer_ns();
+    const unsigned long long last = ld_cg(q.dpoll);
+    if (now - last < (unsigned long long)kServePollNs || atomicCAS(q.dpoll, last, now) != last) return;
+    const unsigned long long t = ld_acquire_sys(q.tail);
+    const int bud = ld_vol(q.budget);
+    __threadfence();   // what the host wrote before `tail`, before the copy of `tail`
+    atomicMax(q.dtail, t);
+    *reinterpret_cast<volatile int *>(q.dbudget) = bud;
+}
+// Copies the host descriptor of chunk c (ring entry ce) into the device ring;
+// called after a claim from the chunk succeeded, so the chunk is live and
+// its entry stable.  The sequence number is written last.
+__device__ __forceinline__ void serve_mirror(const ServeQueue &q, int ce, long long c) {
+    const ServeDesc *hd = q.desc + ce;
+    ServeDesc *md = q.mdesc + ce;
+    md->start = ld_vol(&hd->start);
+    md->n_cells = ld_vol(&hd->n_cells);
+    md->ld = ld_vol(&hd->ld);
+    md->rho = ld_vol(&hd->rho);
+    md->e = ld_vol(&hd->e);
+    md->T_out = ld_vol(&hd->T_out);
+    md->status = ld_vol(&hd->status);
+    md->dt = ld_vol(&hd->dt);
+    __threadfence();
+    *reinterpret_cast<volatile long long *>(&md->seq) = c;
+}
+// Claims up to k consecutive cells of the current chunk for a warp's free
+// slots: returns how many (0 when none is published or the launch's block
+// budget excludes this block), the first one's virtual number in v0 and the
+// chunk's ring entry in e.  The chunk's size comes from the device copy of
+// its descriptor when one is there, else from host memory (the entry is
+// read after `tail` shows the chunk published and holds it until all of its
+// cells are done), and the first claim makes the copy.  Bounded by the
+// guard; a pass claims, finds the chunk exhausted and moves on, or starts
+// the entry's counter.
+__device__ __forceinline__ int serve_claim(const ServeQueue &q, int k, long long &v0, int &e) {
+    serve_refresh(q);
+    if ((int)blockIdx.x >= ld_cg(q.dbudget)) return 0;
+    long long c = (long long)ld_cg(q.chunk);
+    const unsigned long long tail = (unsigned long long)ld_acquire_gpu(reinterpret_cast<const long long *>(q.dtail));
+    // chunks published: the last one's real cells end at `tail`
+    const long long nch = (long long)((tail + (1ULL << kServeChunkLog) - 1) >> kServeChunkLog);
 #pragma unroll 1
-    for (int guard = 0; guard < q.cap; ++guard, ++s) {
-        const ServeDesc *d = q.desc + (s % q.cap);
-        if (ld_vol(&d->seq) != s) continue;
-        const long long st = ld_vol(&d->start), nc = ld_vol(&d->n_cells);
-        if (v >= st && v < st + nc) {
-            cell = v - st;
-            return (int)(s % q.cap);
+    for (int guard = 0; guard < 64 && c < nch; ++guard) {
+        const int ce = (int)(c % q.cap);
+        const bool mirrored = ld_acquire_gpu(&q.mdesc[ce].seq) == c;
+        long long nc;
+        if (mirrored) {
+            nc = ld_cg(&q.mdesc[ce].n_cells);
+        } else {
+            const ServeDesc *d = q.desc + ce;
+            if (ld_vol(&d->seq) != c) {
+                // a stale chunk number (finished, its entry reused since)
+                // moves on; an entry out of order is an error
+                const long long c2 = (long long)ld_cg(q.chunk);
+                if (c2 != c) {
+                    c = c2;
+                    continue;
+                }
+                atomicExch(q.error, 1);
+                return 0;
+            }
+            nc = ld_vol(&d->n_cells);
         }
+        // the entry's counter: the first claim of this lap of the ring
+        // starts it (the counter is never reset otherwise, so claims that
+        // arrive after a chunk is handed out only find it exhausted)
+        const long long lap = c / q.cap;
+        constexpr unsigned long long kCount = (1ULL << kClaimLapShift) - 1;
+        unsigned long long r = ld_cg(q.claimed + ce);
+        if ((long long)(r >> kClaimLapShift) < lap) {
+            atomicCAS(q.claimed + ce, r, (unsigned long long)lap << kClaimLapShift);
+            continue;
+        }
+        if ((long long)(r >> kClaimLapShift) > lap) {
+            // the entry has moved on: a stale chunk number
+            const long long c2 = (long long)ld_cg(q.chunk);
+            if (c2 != c) {
+                c = c2;
+                continue;
+            }
+            atomicExch(q.error, 1);
+            return 0;
+        }
+        if ((long long)(r & kCount) < nc) {
+            r = atomicAdd(q.claimed + ce, (unsigned long long)k);
+            const long long off = (long long)(r & kCount);
+            if ((long long)(r >> kClaimLapShift) != lap) {
+                // only a claim through a chunk number older than a whole
+                // ring of chunks gets here
+                atomicExch(q.error, 1);
+                return 0;
+            }
+            if (off < nc) {
+                if (!mirrored) serve_mirror(q, ce, c);
+                const long long cnt = min((long long)k, nc - off);
+                v0 = (c << kServeChunkLog) + off;
+                e = ce;
+                if ((v0 >> 5) != ((v0 + cnt) >> 5))
+                    *reinterpret_cast<volatile unsigned long long *>(q.front) = (unsigned long long)(v0 + cnt);
+                return (int)cnt;
+            }
+        }
+        // the chunk is handed out: on to the next
+        atomicMax(q.chunk, (unsigned long long)(c + 1));
+        ++c;
     }
-    atomicExch(q.error, 1);
-    return -1;
+    return 0;
 }
 // Counts a finished cell of ring entry e (lane 0 of its slot); the slot that
 // finishes the request's last cell resets the entry's counters for the next
@@ -1108,8 +1207,8 @@ __device__ __forceinline__ void serve_cell_done(const ServeQueue &q, int e) {
     atomicMax(q.t_last + e, globaltimer_ns());
     __threadfence();
     const unsigned long long prev = atomicAdd(q.done + e, 1ULL);
-    const ServeDesc *d = q.desc + e;
-    if ((long long)prev + 1 == ld_vol(&d->n_cells)) {
+    const ServeDesc *d = q.mdesc + e;
+    if ((long long)prev + 1 == ld_cg(&d->n_cells)) {
         const unsigned long long tf = atomicExch(q.t_first + e, ~0ULL);
         const unsigned long long tl = atomicExch(q.t_last + e, 0ULL);
         atomicExch(q.done + e, 0ULL);
@@ -1118,7 +1217,7 @@ __device__ __forceinline__ void serve_cell_done(const ServeQueue &q, int e) {
         f->t_first = tf;
         f->t_last = tl;
         __threadfence_system();
-        f->seq = ld_vol(&d->seq);
+        f->seq = ld_cg(&d->seq);
     }
 }
 
@@ -1159,9 +1258,9 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
     auto emit = [&](int code, double Tv) {
         if (sl == 0) {
             if constexpr (Q) {
-                const ServeDesc *d = b.queue.desc + qe;
-                int *st = ld_vol(&d->status);
-                double *to = ld_vol(&d->T_out);
+                const ServeDesc *d = b.queue.mdesc + qe;
+                int *st = ld_cg(&d->status);
+                double *to = ld_cg(&d->T_out);
                 if (st) st[cell] = code;
                 if (to) to[cell] = Tv;
                 serve_cell_done(b.queue, qe);
@@ -1205,6 +1304,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
 #pragma unroll 1
     for (;;) {
         // refill free slots and settle every pending temperature recovery
+        bool q_dry = false;   // request-server mode: a claim this trip found no cell
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             long long got = -1;
@@ -1212,25 +1312,43 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
             const double *rho_in = b.rho, *e_in = b.e;
             long long ld_in = b.ld;
             if constexpr (Q) {
-                // claim the next published cell, find its request
-                int e = -1;
-                if (state == kFree && sl == 0) {
-                    got = serve_claim(b.queue);
-                    if (got >= 0) {
-                        e = serve_find(b.queue, got, cell);
-                        if (e >= 0) atomicMin(b.queue.t_first + e, globaltimer_ns());
+                // the warp's free slots take consecutive cells of one chunk,
+                // claimed by lane 0, which reads the chunk's descriptor once
+                const unsigned lead = __ballot_sync(kFull, state == kFree && sl == 0);
+                int cnt = 0, e = -1;
+                long long v0 = 0;
+                double cdt = 0.0;   // the chunk's dt (a slot's own sdt changes only when it loads)
+                if (lane == 0 && lead && !q_dry) {
+                    cnt = serve_claim(b.queue, __popc(lead), v0, e);
+                    if (cnt > 0) {
+                        const ServeDesc *d = b.queue.mdesc + e;
+                        rho_in = ld_cg(&d->rho);
+                        e_in = ld_cg(&d->e);
+                        ld_in = ld_cg(&d->ld);
+                        cdt = ld_cg(&d->dt);
+                        atomicMin(b.queue.t_first + e, globaltimer_ns());
                     }
                 }
-                e = __shfl_sync(kFull, e, slot * G);
-                cell = __shfl_sync(kFull, cell, slot * G);
-                loading = state == kFree && e >= 0;
-                if (loading) {
-                    qe = e;
-                    const ServeDesc *d = b.queue.desc + qe;
-                    rho_in = ld_vol(&d->rho);
-                    e_in = ld_vol(&d->e);
-                    ld_in = ld_vol(&d->ld);
-                    sdt = ld_vol(&d->dt);
+                cnt = __shfl_sync(kFull, cnt, 0);
+                if (lead && cnt == 0) q_dry = true;
+                loading = false;
+                if (cnt > 0) {
+                    e = __shfl_sync(kFull, e, 0);
+                    v0 = __shfl_sync(kFull, v0, 0);
+                    rho_in = reinterpret_cast<const double *>(
+                        __shfl_sync(kFull, reinterpret_cast<unsigned long long>(rho_in), 0));
+                    e_in = reinterpret_cast<const double *>(
+                        __shfl_sync(kFull, reinterpret_cast<unsigned long long>(e_in), 0));
+                    ld_in = __shfl_sync(kFull, ld_in, 0);
+                    cdt = __shfl_sync(kFull, cdt, 0);
+                    // this slot's rank among the warp's free slots
+                    const int rank = __popc(lead & ((1u << (slot * G)) - 1u));
+                    loading = state == kFree && rank < cnt;
+                    if (loading) {
+                        qe = e;
+                        sdt = cdt;
+                        cell = (v0 & ((1LL << kServeChunkLog) - 1)) + rank;
+                    }
                 }
             } else {
                 if (state == kFree && sl == 0) got = (long long)atomicAdd(b.work_counter, 1ULL);
@@ -1334,10 +1452,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
                         double *rho_out = b.rho, *e_out = b.e;
                         long long ld_out = b.ld;
                         if constexpr (Q) {
-                            const ServeDesc *d = b.queue.desc + qe;
-                            rho_out = ld_vol(&d->rho);
-                            e_out = ld_vol(&d->e);
-                            ld_out = ld_vol(&d->ld);
+                            const ServeDesc *d = b.queue.mdesc + qe;
+                            rho_out = ld_cg(&d->rho);
+                            e_out = ld_cg(&d->e);
+                            ld_out = ld_cg(&d->ld);
                         }
 #pragma unroll 1
                         for (int i = sl; i < n; i += G) {
@@ -1368,8 +1486,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 2) be_kernel(DeviceMech m, S
                 if (__all_sync(kFull, state == kFree)) {
                     const unsigned long long now = globaltimer_ns();
                     if (idle_since == 0) idle_since = now;
+                    if (lane == 0) serve_refresh(b.queue);
+                    __syncwarp();
                     // one decision for the whole warp
-                    if (__any_sync(kFull, (int)blockIdx.x >= ld_vol(b.queue.budget) ||
+                    if (__any_sync(kFull, (int)blockIdx.x >= ld_cg(b.queue.dbudget) ||
                                               now - idle_since > (unsigned long long)b.queue.linger_ns))
                         break;
                     __nanosleep(20000);

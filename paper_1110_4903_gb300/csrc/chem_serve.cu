@@ -103,7 +103,8 @@ constexpr int kRing = 1024;
 // Cells per published chunk: requests are published in chunks, interleaved
 // across the lane's active requests (pump), so a request that arrives while a
 // large one runs is claimed within one window, not after all of its cells.
-constexpr int64_t kChunkCells = 1024;
+// Chunk seq owns the virtual cells from seq * kChunkCells on.
+constexpr int64_t kChunkCells = 1LL << kServeChunkLog;
 // Kernel instances per lane at once (each with its own block budget).
 constexpr int kMaxInstances = 4;
 // A warp with no work leaves after this long at most.
@@ -115,7 +116,13 @@ constexpr double kIdleRetireS = 2e-3;
 // lane's persistent kernel runs may wait for that kernel.
 constexpr int kMaxLanes = 16;
 constexpr size_t kLaneHostBytes = sizeof(ServeDesc) * kRing + sizeof(ServeDone) * kRing + 4 * 64;
-constexpr size_t kLaneDevBytes = 256 + 3 * sizeof(unsigned long long) * kRing;
+// device memory of a lane: the chunk being handed out, error, the copies of
+// tail, the poll times and the budgets (one per instance) in the first 256
+// bytes; per ring entry the cells done, first claim, last completion and the
+// claim counter; the descriptor copies
+constexpr size_t kLaneDevBytes = 256 + 4 * sizeof(unsigned long long) * kRing + sizeof(ServeDesc) * kRing;
+static_assert(192 + kMaxInstances * (sizeof(unsigned long long) + sizeof(int)) <= 256, "lane header");
+static_assert((256 + 4 * sizeof(unsigned long long) * kRing) % 64 == 0, "descriptor copies aligned");
 
 enum Phase { kQueued = 0, kStaging = 1, kPublished = 2, kReturning = 3, kFinished = 4 };
 
@@ -158,20 +165,22 @@ struct Lane {
     ServeDone *fin = nullptr;
     unsigned long long *tail = nullptr;
     unsigned long long *front = nullptr;   // a recent claim, written by the kernel
-    long long *oldest = nullptr;
     int *budgets = nullptr;          // [kMaxInstances]
     ServeDesc *d_desc = nullptr;
     ServeDone *d_fin = nullptr;
     unsigned long long *d_tail = nullptr;
     unsigned long long *d_front = nullptr;
-    long long *d_oldest = nullptr;
     int *d_budgets = nullptr;
     // device memory: next, error, then done / t_first / t_last per entry
     void *dev = nullptr;
-    unsigned long long *next = nullptr, *done = nullptr, *t_first = nullptr, *t_last = nullptr;
+    unsigned long long *chunk = nullptr, *done = nullptr, *t_first = nullptr, *t_last = nullptr;
+    unsigned long long *claimed = nullptr;                   // [kRing]
+    unsigned long long *dtail = nullptr, *dpoll = nullptr;   // dpoll [kMaxInstances]
+    int *dbudget = nullptr;                                  // [kMaxInstances]
+    ServeDesc *mdesc = nullptr;                              // [kRing]
     int *error = nullptr;
     long long next_seq = 0;
-    unsigned long long published = 0;
+    unsigned long long published = 0;        // virtual cells of the published chunks
     long long window = 0;                     // published cells kept ahead of the claims
     std::deque<uint64_t> rr;                  // requests with cells still to publish
     std::map<long long, uint64_t> inflight;   // chunk seq -> ticket, published and unfinished
@@ -247,7 +256,6 @@ int get_lane(chem_server_s *S, Handle *h, int prec, int &idx) {
     L->fin = reinterpret_cast<ServeDone *>(hp + sizeof(ServeDesc) * kRing);
     const size_t toff = sizeof(ServeDesc) * kRing + sizeof(ServeDone) * kRing;
     L->tail = reinterpret_cast<unsigned long long *>(hp + toff);
-    L->oldest = reinterpret_cast<long long *>(hp + toff + 64);
     L->budgets = reinterpret_cast<int *>(hp + toff + 128);
     L->front = reinterpret_cast<unsigned long long *>(hp + toff + 192);
     for (int i = 0; i < kRing; ++i) {
@@ -257,23 +265,29 @@ int get_lane(chem_server_s *S, Handle *h, int prec, int &idx) {
     L->d_desc = reinterpret_cast<ServeDesc *>(dp);
     L->d_fin = reinterpret_cast<ServeDone *>(dp + sizeof(ServeDesc) * kRing);
     L->d_tail = reinterpret_cast<unsigned long long *>(dp + toff);
-    L->d_oldest = reinterpret_cast<long long *>(dp + toff + 64);
     L->d_budgets = reinterpret_cast<int *>(dp + toff + 128);
     L->d_front = reinterpret_cast<unsigned long long *>(dp + toff + 192);
     // cells kept published ahead of the claims: one and a half grids of slots
     const long long slots = (long long)L->cfg->grid * (L->cfg->block / 32) * (32 / L->cfg->G);
     L->window = std::max<long long>(slots + slots / 2, kChunkCells);
     char *d = S->lane_dev + (size_t)li * kLaneDevBytes;
-    L->next = reinterpret_cast<unsigned long long *>(d);
+    L->chunk = reinterpret_cast<unsigned long long *>(d);
     L->error = reinterpret_cast<int *>(d + 64);
+    L->dtail = reinterpret_cast<unsigned long long *>(d + 128);
+    L->dpoll = reinterpret_cast<unsigned long long *>(d + 192);
+    L->dbudget = reinterpret_cast<int *>(d + 192 + kMaxInstances * sizeof(unsigned long long));
     L->done = reinterpret_cast<unsigned long long *>(d + 256);
     L->t_first = L->done + kRing;
     L->t_last = L->t_first + kRing;
+    L->claimed = L->t_last + kRing;
+    L->mdesc = reinterpret_cast<ServeDesc *>(L->claimed + kRing);
     // counters on the lane's first stream, ahead of its first kernel there;
     // instances on its other streams wait for them
     cudaError_t ce = cudaMemsetAsync(d, 0, kLaneDevBytes, L->streams[0]);
     if (ce == cudaSuccess)
         ce = cudaMemsetAsync(L->t_first, 0xff, sizeof(unsigned long long) * kRing, L->streams[0]);
+    // no descriptor copies yet: every sequence number -1
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(L->mdesc, 0xff, sizeof(ServeDesc) * kRing, L->streams[0]);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(L->streams[0]);
     if (ce != cudaSuccess) {
         delete L;
@@ -310,9 +324,13 @@ int launch_instance(chem_server_s *S, Lane *L, int grid) {
     b.queue.fin = L->d_fin;
     b.queue.tail = L->d_tail;
     b.queue.front = L->d_front;
-    b.queue.oldest = L->d_oldest;
     b.queue.budget = L->d_budgets + cell;
-    b.queue.next = L->next;
+    b.queue.mdesc = L->mdesc;
+    b.queue.dtail = L->dtail;
+    b.queue.dbudget = L->dbudget + cell;
+    b.queue.dpoll = L->dpoll + cell;
+    b.queue.chunk = L->chunk;
+    b.queue.claimed = L->claimed;
     b.queue.done = L->done;
     b.queue.t_first = L->t_first;
     b.queue.t_last = L->t_last;
@@ -321,7 +339,11 @@ int launch_instance(chem_server_s *S, Lane *L, int grid) {
     b.queue.error = L->error;
     void *args[] = {&m, &o, &b};
     cudaStream_t st = L->streams[cell];
-    ce = cudaLaunchKernel(L->cfg->fn, dim3((unsigned)grid), dim3(L->cfg->block), args, L->cfg->smem, st);
+    // the instance's budget copy, ahead of it on its stream (the kernel
+    // refreshes it from host memory while it runs)
+    ce = cudaMemcpyAsync(L->dbudget + cell, L->budgets + cell, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaLaunchKernel(L->cfg->fn, dim3((unsigned)grid), dim3(L->cfg->block), args, L->cfg->smem, st);
     if (ce == cudaSuccess) ce = cudaEventRecord(in.ev, st);
     if (ce != cudaSuccess) {
         cudaEventDestroy(in.ev);
@@ -340,7 +362,7 @@ void publish_chunk(Lane *L, Req &q, int64_t c) {
     const int e = (int)(seq % kRing);
     volatile ServeDesc *d = L->desc + e;
     const int64_t p = q.pos;
-    d->start = (long long)L->published;
+    d->start = seq << kServeChunkLog;
     d->n_cells = c;
     d->ld = q.r.host ? q.r.n_cells : (q.r.ld ? q.r.ld : q.r.n_cells);
     d->rho = q.d_rho + p;
@@ -348,12 +370,13 @@ void publish_chunk(Lane *L, Req &q, int64_t c) {
     d->T_out = q.d_T ? q.d_T + p : nullptr;
     d->status = q.d_st ? q.d_st + p : nullptr;
     d->dt = q.r.dt;
-    if (L->inflight.empty()) *reinterpret_cast<volatile long long *>(L->oldest) = seq;
     std::atomic_thread_fence(std::memory_order_seq_cst);
     d->seq = seq;
     std::atomic_thread_fence(std::memory_order_seq_cst);
-    L->published += (unsigned long long)c;
-    *reinterpret_cast<volatile unsigned long long *>(L->tail) = L->published;
+    // the chunk's real cells become claimable; its unused numbers up to the
+    // next chunk's start are skipped by the claims
+    L->published = (unsigned long long)(seq + 1) << kServeChunkLog;
+    *reinterpret_cast<volatile unsigned long long *>(L->tail) = ((unsigned long long)seq << kServeChunkLog) + c;
     std::atomic_thread_fence(std::memory_order_seq_cst);
     q.pos += c;
     q.chunks_out++;
@@ -471,8 +494,6 @@ bool poll_lanes(chem_server_s *S) {
                 finish(S, q, CHEM_REQ_DONE, CHEM_OK);
             }
         }
-        const long long oldest = L->inflight.empty() ? L->next_seq : L->inflight.begin()->first;
-        *reinterpret_cast<volatile long long *>(L->oldest) = oldest;
         pump(S, L);
     }
     return any;
