@@ -97,7 +97,8 @@ typedef struct chem_options {
     int32_t div_check;        /* 1: abandon a substep whose Newton norm stops falling */
     int32_t lanes_per_cell;   /* 0 = chosen by the library; else 2, 4, 8, 16 or 32 */
     int32_t autotune;         /* 1: time the lane choices once and keep the best */
-    int64_t hbm_budget_bytes; /* serving: device bytes requests may hold (0 = 50% of free) */
+    int64_t hbm_budget_bytes; /* not used by the step calls (validated: >= 0); the request
+                                 server's budget is chem_server_options.hbm_budget_bytes */
     int32_t max_newton_mixed; /* Newton iterations per attempt on the CHEM_MIXED path, whose
                                  FP32 LU makes convergence linear; 1..1000 */
     double  conv_kappa;       /* > 0: also converged when the contraction theta = norm_k/norm_k-1 < 1
