@@ -345,11 +345,23 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     // kernels eliminate the energy unknown, so no energy row is gathered)
     struct Term { int j; double c; int nu; };
     std::vector<std::vector<Term>> lists((size_t)ns * ns);
+    // nu as signed powers of two (the packed words carry a coefficient's
+    // sign and exponent bits, exact for those; any other nu, none in the
+    // mechanisms at hand, becomes one term per binary digit)
+    auto pow2_parts = [](int v) {
+        std::vector<int> out;
+        const int a = v < 0 ? -v : v;
+        for (int b = 0; b < 31; ++b)
+            if (a & (1 << b)) out.push_back(v < 0 ? -(1 << b) : (1 << b));
+        return out;
+    };
     for (int j = 0; j < t.nD; ++j) {
         const int r = ents[j].r, k = ents[j].k;
         for (int s = 0; s < ns; ++s) {
             const int v = net(r, s);
-            if (v != 0) lists[(size_t)s * ns + k].push_back({j, v * d->molar_mass[s], v});
+            if (v == 0) continue;
+            // the FP64 lists keep nu_rs M_s whole; the FP32 lists, the parts
+            lists[(size_t)s * ns + k].push_back({j, v * d->molar_mass[s], v});
         }
     }
     // the species entries, longest list first; the FP64 kernel's lists
@@ -369,8 +381,10 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         for (const auto &tm : lists[idx]) {
             t.j_d.push_back(tm.j);
             t.j_c.push_back(tm.c);
-            t.j_d32.push_back(tm.j);
-            t.j_nu.push_back(tm.nu);
+            for (int part : pow2_parts(tm.nu)) {
+                t.j_d32.push_back(tm.j);
+                t.j_nu.push_back(part);
+            }
         }
         t.j_ptr.push_back((int)t.j_d.size());
         t.j_ptr32.push_back((int)t.j_d32.size());
@@ -383,11 +397,13 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         for (int r = 0; r < nr; ++r) {
             const int v = net(r, s);
             if (v == 0) continue;
-            t.sp_r.push_back(r);
-            t.sp_nui.push_back(v);
-            if (++cnt == kChunk) {
-                t.it_ptr.push_back((int)t.sp_r.size());
-                cnt = 0;
+            for (int part : pow2_parts(v)) {
+                t.sp_r.push_back(r);
+                t.sp_nui.push_back(part);
+                if (++cnt == kChunk) {
+                    t.it_ptr.push_back((int)t.sp_r.size());
+                    cnt = 0;
+                }
             }
         }
         if (cnt > 0) t.it_ptr.push_back((int)t.sp_r.size());
@@ -411,10 +427,24 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
     for (int j = 0; j < t.nD; ++j) {
         t.d_pk.push_back(make_int2(t.d_i0[j], t.d_i1[j]));
     }
-    // a term's word: D index (or reaction) in bits 0..23, nu_rs in 24..31
-    auto word = [](int i, int nu) { return (unsigned)i | ((unsigned)(nu & 0xff) << 24); };
-    for (size_t e = 0; e < t.j_d32.size(); ++e) t.j_w.push_back(word(t.j_d32[e], t.j_nu[e]));
-    for (size_t e = 0; e < t.sp_r.size(); ++e) t.sp_w.push_back(word(t.sp_r[e], t.sp_nui[e]));
+    // a term's word (nu a signed power of two): the FP32 gather's carries
+    // the sign and exponent bits of (float)nu over the D index (bits 0..22),
+    // the species lists' those of (double)nu over the reaction (bits 0..19),
+    // so one mask gives the coefficient exactly
+    auto fword = [](int i, int nu) {
+        const float f = (float)nu;
+        unsigned b;
+        memcpy(&b, &f, 4);
+        return (b & 0xff800000u) | (unsigned)i;
+    };
+    auto dword = [](int r, int nu) {
+        const double x = (double)nu;
+        unsigned long long b;
+        memcpy(&b, &x, 8);
+        return ((unsigned)(b >> 32) & 0xfff00000u) | (unsigned)r;
+    };
+    for (size_t e = 0; e < t.j_d32.size(); ++e) t.j_w.push_back(fword(t.j_d32[e], t.j_nu[e]));
+    for (size_t e = 0; e < t.sp_r.size(); ++e) t.sp_w.push_back(dword(t.sp_r[e], t.sp_nui[e]));
     // the gather layouts for each lane count (chem_internal.h): list p on
     // lane p % G of pass p / G, its q-th term at base(pass) + q G + lane
     // With `bank` (the shared-memory bank each term's operand sits in), the

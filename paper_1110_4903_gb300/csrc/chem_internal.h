@@ -90,11 +90,14 @@ constexpr int kLogTab = 128;
 //     j_meta[p]   = {first word of entry p, k | s << 8 | terms << 16}
 //     j_d, j_c    = D index and coefficient nu_rs M_s (FP64 kernel)
 //     j_meta32[p] = as j_meta, with the FP32 lists' own word positions
-//     j_w         = D index | nu_rs << 24 (FP32 kernel: the row's M_s
-//                   multiplies the sum; terms ordered across the lanes of a
-//                   pass for distinct shared-memory banks)
+//     j_w         = D index (bits 0..22) | the sign and exponent bits of
+//                   (float)nu_rs (FP32 kernel: the row's M_s multiplies the
+//                   sum; terms ordered across the lanes of a pass for
+//                   distinct shared-memory banks)
 //   it_meta[i] = {first word of item i, entries}
-//   sp_w       = r | nu_rs << 24
+//   sp_w       = r (bits 0..19) | the sign and exponent bits of (double)nu_rs
+// (nu_rs a signed power of two in the words: any other nu_rs is split into
+// one term per binary digit)
 struct GatherLayout {
     const int2 *j_meta;
     const int2 *j_meta32;

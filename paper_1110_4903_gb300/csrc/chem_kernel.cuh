@@ -227,13 +227,16 @@ static __device__ __noinline__ double exp_outside(double x) { return exp(x); }
 __device__ __forceinline__ float small_int_to_float(int v) {
     return __int_as_float(0x4B400000 + v) - 12582912.0f;
 }
-// A nonzero signed integer (|v| < 2^20) as a double from integer operations
-// only (sign, biased exponent of the top bit, the bits below it), exact.
-__device__ __forceinline__ double small_int_to_double(int v) {
-    const unsigned a = v < 0 ? (unsigned)-v : (unsigned)v;
-    const int e = 31 - __clz(a);
-    const unsigned hi = (v < 0 ? 0x80000000u : 0u) | ((unsigned)(1023 + e) << 20) | ((a << (20 - e)) & 0xfffffu);
-    return __hiloint2double((int)hi, 0);
+// The coefficient of a packed list word (a signed power of two stored as
+// the sign and exponent bits of its double, over the reaction index in bits
+// 0..19) as a double and as a float, by integer operations only: the
+// float's exponent is the double's less 1023 - 127.
+__device__ __forceinline__ double word_nu_double(unsigned wv) {
+    return __hiloint2double((int)(wv & 0xfff00000u), 0);
+}
+__device__ __forceinline__ float word_nu_float(unsigned wv) {
+    const unsigned hi = wv & 0xfff00000u;
+    return __int_as_float((int)((hi & 0x80000000u) | (((hi & 0x7ff00000u) - 0x38000000u) << 3)));
 }
 
 // exp by the table-driven reduction of P. T. P. Tang, ACM TOMS 15(2), 1989:
@@ -725,9 +728,9 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             if (q < im.y) {
                 const int e = im.x + q * G;
                 const unsigned wv = __ldg(gl.sp_w + e);
-                const int r = (int)(wv & 0xffffffu);
-                const double nu = small_int_to_double((int)wv >> 24);   // nu_rs != 0 in a list
-                const JT nuj = f32 ? (JT)small_int_to_float((int)wv >> 24) : (JT)nu;
+                const int r = (int)(wv & 0xfffffu);
+                const double nu = word_nu_double(wv);   // nu_rs != 0 in a list
+                const JT nuj = f32 ? (JT)word_nu_float(wv) : (JT)nu;
                 sq = fma(nu, sm.Q[r], sq);
                 sdq += nuj * sm.dQdT[r];
                 if (r < m.ntb) squ += nuj * sm.qtb[r];
@@ -862,13 +865,14 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         int e = meta.x, q = 0;
         if (f32) {
             // M_s sum nu_rs D_rk
-            auto coef = [](unsigned wv) -> JT { return (JT)small_int_to_float((int)wv >> 24); };
+            // (the word's top nine bits are those of the float coefficient)
+            auto coef = [](unsigned wv) -> JT { return (JT)__int_as_float((int)(wv & 0xff800000u)); };
 #pragma unroll 1
             for (; q + 4 <= len; q += 4, e += 4 * G) {
                 const unsigned w0 = __ldg(gl.j_w + e), w1 = __ldg(gl.j_w + e + G), w2 = __ldg(gl.j_w + e + 2 * G),
                                w3 = __ldg(gl.j_w + e + 3 * G);
-                const JT v0 = Dv[w0 & 0xffffffu], v1 = Dv[w1 & 0xffffffu], v2 = Dv[w2 & 0xffffffu],
-                         v3 = Dv[w3 & 0xffffffu];
+                const JT v0 = Dv[w0 & 0x7fffffu], v1 = Dv[w1 & 0x7fffffu], v2 = Dv[w2 & 0x7fffffu],
+                         v3 = Dv[w3 & 0x7fffffu];
                 a0 = fma(coef(w0), v0, a0);
                 a1 = fma(coef(w1), v1, a1);
                 a0 = fma(coef(w2), v2, a0);
@@ -877,7 +881,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
 #pragma unroll 1
             for (; q < len; ++q, e += G) {
                 const unsigned wv = __ldg(gl.j_w + e);
-                a0 = fma(coef(wv), Dv[wv & 0xffffffu], a0);
+                a0 = fma(coef(wv), Dv[wv & 0x7fffffu], a0);
             }
             // (D entries scaled by M_k: J_sk = w_s dT/drho_k + (u_s + M_s sum) / M_k)
             J = fma(invMk, fma((JT)__ldg(m.spf + s * kSpStride), a0 + a1, sm.u[s]), J);
