@@ -123,7 +123,7 @@ struct DeviceMech {
     const double *tpoly;        // [12][2][ns] energy and heat-capacity polynomials
     const float *tpoly_f;       // [8][2][ns] heat-capacity polynomial in FP32
     const double *sp;           // [ns][4]
-    const double *rxn_d;        // [nr][4]
+    const double *rxn_d;        // [nr][4] ln A (SI), beta, E/R, sum nu
     const int *rxn_f;           // [nr][2]
     const int *eff_ptr;         // [nr+1] CSR of efficiency corrections of +M reactions
     const int *eff_sp;          //        species

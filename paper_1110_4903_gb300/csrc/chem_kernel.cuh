@@ -97,10 +97,11 @@ struct Grp {
         }
     }
     // largest key, lowest index on ties
-    __device__ __forceinline__ static void argmax(unsigned long long &k, int &i) {
+    template <typename K>
+    __device__ __forceinline__ static void argmax(K &k, int &i) {
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
-            const unsigned long long k2 = __shfl_xor_sync(kFull, k, o);
+            const K k2 = __shfl_xor_sync(kFull, k, o);
             const int i2 = __shfl_xor_sync(kFull, i, o);
             if (k2 > k || (k2 == k && i2 < i)) {
                 k = k2;
@@ -160,21 +161,18 @@ __device__ __forceinline__ bool finite_bits(double v) {
 // Argmax over a whole warp (one cell per warp) with redux.sync: the largest
 // key, the lowest index on ties, as the shuffle tree gives it.  FP64 keys
 // take the high word, then the low word among the lanes holding the high
-// maximum; FP32 keys (abs bits << 29) fit one word.
-template <typename JT>
+// maximum; FP32 keys fit one word.
 __device__ __forceinline__ void warp_argmax(unsigned long long &k, int &i) {
-    if (sizeof(JT) == 4) {
-        const unsigned k32 = (unsigned)(k >> 29);
-        const unsigned m = __reduce_max_sync(kFull, k32);
-        i = (int)__reduce_min_sync(kFull, k32 == m ? (unsigned)i : 0xffffffffu);
-        k = (unsigned long long)m << 29;
-    } else {
-        const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
-        const unsigned mhi = __reduce_max_sync(kFull, hi);
-        const unsigned mlo = __reduce_max_sync(kFull, hi == mhi ? lo : 0u);
-        i = (int)__reduce_min_sync(kFull, (hi == mhi && lo == mlo) ? (unsigned)i : 0xffffffffu);
-        k = ((unsigned long long)mhi << 32) | mlo;
-    }
+    const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+    const unsigned mhi = __reduce_max_sync(kFull, hi);
+    const unsigned mlo = __reduce_max_sync(kFull, hi == mhi ? lo : 0u);
+    i = (int)__reduce_min_sync(kFull, (hi == mhi && lo == mlo) ? (unsigned)i : 0xffffffffu);
+    k = ((unsigned long long)mhi << 32) | mlo;
+}
+__device__ __forceinline__ void warp_argmax(unsigned &k, int &i) {
+    const unsigned m = __reduce_max_sync(kFull, k);
+    i = (int)__reduce_min_sync(kFull, k == m ? (unsigned)i : 0xffffffffu);
+    k = m;
 }
 
 // |v| as an ordered integer key (NaN maps to 0 so it is never the pivot).
@@ -182,15 +180,15 @@ __device__ __forceinline__ unsigned long long abs_key(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
     return b > 0x7ff0000000000000ULL ? 0ULL : b;
 }
-__device__ __forceinline__ unsigned long long abs_key(float v) {
+__device__ __forceinline__ unsigned abs_key(float v) {
     const unsigned b = __float_as_uint(v) & 0x7fffffffu;
-    // widen to the double key scale (order is all that matters)
-    return b > 0x7f800000u ? 0ULL : ((unsigned long long)b << 29);
+    return b > 0x7f800000u ? 0u : b;
 }
-__device__ __forceinline__ bool key_is_inf(unsigned long long k, double) { return k >= 0x7ff0000000000000ULL; }
-__device__ __forceinline__ bool key_is_inf(unsigned long long k, float) {
-    return k >= ((unsigned long long)0x7f800000u << 29);
-}
+__device__ __forceinline__ bool key_is_inf(unsigned long long k) { return k >= 0x7ff0000000000000ULL; }
+__device__ __forceinline__ bool key_is_inf(unsigned k) { return k >= 0x7f800000u; }
+// the pivot key of a matrix type: 64 bits for FP64, 32 for FP32
+template <typename JT>
+using PivotKey = decltype(abs_key(JT(0)));
 
 // Reciprocal: the hardware approximation r refined with its residual
 // e = 1 - a r as r (1 + e + e^2), whose error is e^3 (the approximation is
@@ -913,21 +911,21 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     bool sing = false;
 #pragma unroll 1
     for (int j = 0; j < N; ++j) {
-        unsigned long long best = 0;
+        PivotKey<JT> best = 0;
         int bi = N;
 #pragma unroll 1
         for (int i = j + sl; i < N; i += G) {
-            const unsigned long long kk = abs_key(sm.A[ix(i, j)]);
+            const PivotKey<JT> kk = abs_key(sm.A[ix(i, j)]);
             if (bi == N || kk > best) {
                 best = kk;
                 bi = i;
             }
         }
         if constexpr (G == 32)
-            warp_argmax<JT>(best, bi);
+            warp_argmax(best, bi);
         else
             Grp<G>::argmax(best, bi);
-        if (best == 0 || key_is_inf(best, JT(0))) sing = true;
+        if (best == 0 || key_is_inf(best)) sing = true;
         if (bi != j && bi < N) {
 #pragma unroll 1
             for (int k = j + sl; k <= N; k += G) {
@@ -981,14 +979,38 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     }
     __syncwarp();
     // back substitution, U delta = y
+    if constexpr (f32 && G == 32) {
+        // one cell per warp (N <= 64): lane l keeps rows l and l + 32 of the
+        // right-hand side in registers, and each solved entry reaches the
+        // lanes by a shuffle instead of shared memory and two warp barriers
+        float y0 = sl < N ? sm.A[ix(sl, N)] : 0.f, y1 = sl + 32 < N ? sm.A[ix(sl + 32, N)] : 0.f;
 #pragma unroll 1
-    for (int j = N - 1; j >= 0; --j) {
-        const JT dj = sm.A[ix(j, N)] * sm.A[ix(j, j)];
+        for (int j = N - 1; j >= 0; --j) {
+            const float yj = __shfl_sync(kFull, j < 32 ? y0 : y1, j & 31);
+            const float dj = yj * sm.A[ix(j, j)];
+            if (sl == (j & 31)) {
+                if (j < 32)
+                    y0 = dj;
+                else
+                    y1 = dj;
+            }
+            if (sl < j) y0 = fmaf(-sm.A[ix(sl, j)], dj, y0);
+            if (sl + 32 < j) y1 = fmaf(-sm.A[ix(sl + 32, j)], dj, y1);
+        }
         __syncwarp();
-        if (sl == 0) sm.A[ix(j, N)] = dj;
+        if (sl < N) sm.A[ix(sl, N)] = y0;
+        if (sl + 32 < N) sm.A[ix(sl + 32, N)] = y1;
+        __syncwarp();
+    } else {
 #pragma unroll 1
-        for (int i = sl; i < j; i += G) sm.A[ix(i, N)] -= sm.A[ix(i, j)] * dj;
-        __syncwarp();
+        for (int j = N - 1; j >= 0; --j) {
+            const JT dj = sm.A[ix(j, N)] * sm.A[ix(j, j)];
+            __syncwarp();
+            if (sl == 0) sm.A[ix(j, N)] = dj;
+#pragma unroll 1
+            for (int i = sl; i < j; i += G) sm.A[ix(i, N)] -= sm.A[ix(i, j)] * dj;
+            __syncwarp();
+        }
     }
 
     // 8. update, convergence norm, and the linearised temperature of the
