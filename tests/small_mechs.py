@@ -75,3 +75,21 @@ def third_body_twin(A_cgs=1.0e12):
                                 [(("A", "B"), ("AB",), 0), (("A", "B"), ("AB",), 1)], nasa,
                                 arr_A=[A_cgs, A_cgs * 1e6], arr_beta=[0.3, 0.3],
                                 arr_Ea=[2e4, 2e4])
+
+
+def trimer_chain(A2_cgs=1.0e10, A3_cgs=1.0e12, A3d_cgs=1.0e16, a1=3.0, a6=-800.0):
+    """A, A2, A3 with 2 A <=> A2, A2 + A <=> A3 and 3 A <=> A3: the last gives
+    A a net coefficient of -3, not a power of two.  cp/R = k a1 - (k - 1) and
+    a6 = k a6_A for A_k make every species' per-mass energy the same function
+    of T, so T stays constant.  (The default rates react within a 1e-6 s step
+    but leave Newton's decisions insensitive to rounding: with 1e4 times
+    faster rates a 1-ulp change of the input changed the oracle's own
+    iteration counts in a third of the cells.)"""
+    nasa = np.stack([const_cp(a1, a6, 4.0), const_cp(2 * a1 - 1.0, 2 * a6, 3.0),
+                     const_cp(3 * a1 - 2.0, 3 * a6, 2.5)])
+    comps = {"A": {"H": 1}, "A2": {"H": 2}, "A3": {"H": 3}}
+    return synth.make_mechanism("trimer", ["A", "A2", "A3"], comps, ["H"],
+                                [(("A", "A"), ("A2",), 0), (("A2", "A"), ("A3",), 0),
+                                 (("A", "A", "A"), ("A3",), 0)], nasa,
+                                arr_A=[A2_cgs, A3_cgs, A3d_cgs], arr_beta=[0.0, 0.5, 0.0],
+                                arr_Ea=[0.0, 1.0e4, 0.0])
