@@ -86,6 +86,40 @@ def test_alone_equals_mixed(env):
     srv.close()
 
 
+def test_ring_laps_and_chunk_edges(env):
+    """More chunks than the descriptor ring holds, so its entries and their
+    claim counters go round more than one lap, with request sizes at the
+    chunk edges (1, 1023, 1024, 1025 cells, ...): every result equals a
+    direct step of the same cells, and the queue reports no error."""
+    torch, chem, mechs = env
+    m, h = mechs[9]
+    sizes = [1, 2, 1023, 1024, 1025, 2047, 2048, 2049, 3000]   # 16 chunks a round
+    rho0, e0 = _states(torch, m, max(sizes), seed=77)
+    dt = 1e-7
+    refs = {}
+    for n in sizes:
+        r, e = rho0[:, :n].clone(), e0[:n].clone()
+        h.advance(r, e, dt)
+        refs[n] = (r, e)
+    torch.cuda.synchronize()
+    srv = chem.Server(max_inflight=64)
+    rounds = 72   # 1,152 chunks: past the 1,024 ring entries
+    for k in range(rounds):
+        outs, tickets = [], []
+        for n in sizes:
+            r, e = rho0[:, :n].clone(), e0[:n].clone()
+            tickets.append(srv.submit(h, r, e, dt))
+            outs.append((n, r, e))
+        for t in tickets:
+            assert srv.wait(t).state == chem.REQ_DONE
+        for n, r, e in outs:
+            assert torch.equal(r, refs[n][0]) and torch.equal(e, refs[n][1]), (k, n)
+    st = srv.stats()
+    assert st["failed"] == 0 and st["completed"] == rounds * len(sizes)
+    assert st["queue_errors"] == 0
+    srv.close()
+
+
 def test_small_requests_join_a_running_grid(env):
     """Continuous batching on the device: small requests submitted while a
     large one of the same mechanism runs are claimed by slots that free up
