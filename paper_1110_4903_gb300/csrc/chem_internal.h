@@ -77,9 +77,10 @@ constexpr int kLogTab = 128;
 //   d_pk = {r | nu'_rk << 16 | nu''_rk << 20,
 //           fa | fb << 8 | ba << 16 | bb << 24  (the remaining factors of
 //                d(prod c)/dc_k on each side, sentinel ns if none)}
-//   d_c  = {nu'_rk / M_k, nu''_rk / M_k, (alpha_rk - 1) / M_k} (FP64 kernel)
-//   d_cef = alpha_rk - 1 (FP32 kernel, whose D entries are M_k dQ_r/drho_k:
-//           the 1/M_k is applied once per Jacobian entry in the gather)
+//   d_ce  = alpha_rk - 1 (FP64 kernel), d_cef the same in FP32 (FP32
+//           kernel).  Both kernels' D entries are M_k dQ_r/drho_k, with the
+//           orders nu'_rk, nu''_rk from the descriptor: the 1/M_k is applied
+//           once per Jacobian entry in the gather
 // Gather lists laid out for G lanes per cell.  List p (a Jacobian entry, or
 // an item of a species list) runs in pass p / G on lane p % G; its q-th term
 // sits at word base + q G + lane, where base is the pass's first word, so the
@@ -129,7 +130,7 @@ struct DeviceMech {
     const int *eff_sp;          //        species
     const double *eff_c;        //        alpha - 1
     const int2 *d_pk;           // [nD]
-    const double *d_c;          // [nD][3]
+    const double *d_ce;         // [nD] alpha - 1 (FP64 kernel)
     // Jacobian entries (species rows and columns), longest gather list
     // first, and the species lists (reactions with nu_rs != 0) cut into
     // items of at most kChunk entries; per-G layouts above

@@ -237,6 +237,14 @@ __device__ __forceinline__ float word_nu_float(unsigned wv) {
     return __int_as_float((int)((hi & 0x80000000u) | (((hi & 0x7ff00000u) - 0x38000000u) << 3)));
 }
 
+// A positive integer below 2^20 as a double from integer operations only
+// (biased exponent of its top bit, the bits below it), exact.
+__device__ __forceinline__ double small_pos_int_to_double(int v) {
+    const int e = 31 - __clz(v);
+    const unsigned hi = ((unsigned)(1023 + e) << 20) | (((unsigned)v << (20 - e)) & 0xfffffu);
+    return __hiloint2double((int)hi, 0);
+}
+
 // exp by the table-driven reduction of P. T. P. Tang, ACM TOMS 15(2), 1989:
 // x = (256 k + j) ln2/256 + r with |r| <= ln2/512, exp(x) = 2^k 2^(j/256) e^r,
 // 2^(j/256) from a 256-entry table and e^r - 1 by its degree-4 Taylor
@@ -804,27 +812,24 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
     } else
 #pragma unroll 1
     for (int j = sl; j < m.nD; j += G) {
+        // the FP64 D entries are M_k dQ_r/drho_k as well: integer orders from
+        // the descriptor (exact doubles by integer operations), alpha - 1
+        // from an 8-byte table, and the gather applies the 1/M_k
         const int2 pk = __ldg(m.d_pk + j);
-        const int i0 = pk.x, i1 = pk.y;
-        const int r = i0 & 0xffff;
+        const int r = pk.x & 0xffff, vf = (pk.x >> 16) & 15, vb = (pk.x >> 20) & 15, i1 = pk.y;
         const int fa = i1 & 0xff, fb = (i1 >> 8) & 0xff, ba = (i1 >> 16) & 0xff, bb = (i1 >> 24) & 0xff;
-        JT d;
-        {
-            const double *dc = m.d_c + 3 * (size_t)j;
-            double dd;
-            if (j < m.nD_F) {
-                dd = __ldg(dc) * sm.A1[r] * (sm.c[fa] * sm.c[fb]);
-            } else if (j < m.nD_B) {
-                dd = -__ldg(dc + 1) * sm.A2[r] * (sm.c[ba] * sm.c[bb]);
-            } else if (j < m.nD_FB) {
-                dd = __ldg(dc) * sm.A1[r] * (sm.c[fa] * sm.c[fb]) -
-                     __ldg(dc + 1) * sm.A2[r] * (sm.c[ba] * sm.c[bb]);
-            } else {
-                dd = 0.0;
-            }
-            d = r < m.ntb ? (JT)fma(__ldg(dc + 2), (double)sm.qtb[r], dd) : (JT)dd;
+        double dd;
+        if (j < m.nD_F) {
+            dd = small_pos_int_to_double(vf) * sm.A1[r] * (sm.c[fa] * sm.c[fb]);
+        } else if (j < m.nD_B) {
+            dd = -(small_pos_int_to_double(vb) * sm.A2[r] * (sm.c[ba] * sm.c[bb]));
+        } else if (j < m.nD_FB) {
+            dd = small_pos_int_to_double(vf) * sm.A1[r] * (sm.c[fa] * sm.c[fb]) -
+                 small_pos_int_to_double(vb) * sm.A2[r] * (sm.c[ba] * sm.c[bb]);
+        } else {
+            dd = 0.0;
         }
-        sm.D[j] = d;
+        sm.D[j] = r < m.ntb ? (JT)fma(__ldg(m.d_ce + j), (double)sm.qtb[r], dd) : (JT)dd;
     }
     __syncwarp();
     // the per-reaction arrays are dead from here on; the matrix takes their place
@@ -858,7 +863,7 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
         // (the reduced system's column k: dT/drho_k - e_f,k dT/de)
         const JT dTdrk = f32 ? -sm.esJ[k] * (JT)dTdef : sm.dTdr[k];
-        JT J = f32 ? sm.w[s] * dTdrk : sm.w[s] * dTdrk + sm.u[s] * invMk;
+        JT J = sm.w[s] * dTdrk;
         JT a0 = 0, a1 = 0;
         int e = meta.x, q = 0;
         if (f32) {
@@ -896,7 +901,8 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             }
 #pragma unroll 1
             for (; q < len; ++q, e += G) a0 = fma((JT)__ldg(gl.j_c + e), Dv[__ldg(gl.j_d + e)], a0);
-            J += a0 + a1;
+            // (D entries scaled by M_k: J_sk = w_s dT/drho_k + (u_s + sum) / M_k)
+            J = fma(invMk, sm.u[s] + (a0 + a1), J);
         }
         sm.A[ix(s, k)] = mh * J;
     }
