@@ -279,6 +279,21 @@ def time_path(torch, ch, rho0, e0, T_in, dt, precision, steps, warmup, flush, st
     return tot, ker, stats
 
 
+SERVE_STALL_S = 120.0   # a serving run that completes nothing for this long is an error
+
+
+def _stalled(t_last_done):
+    if time.perf_counter() - t_last_done > SERVE_STALL_S:
+        raise RuntimeError("request server made no progress for %.0f s" % SERVE_STALL_S)
+
+
+def _wait_done(srv, ticket):
+    res = srv.wait(ticket, timeout_us=int(SERVE_STALL_S * 1e6))
+    if res is None:
+        raise RuntimeError("request %d did not finish within %.0f s" % (ticket, SERVE_STALL_S))
+    return res
+
+
 def serving_run(torch, chem, synth, device, n_requests, rate_frac=0.7, budget_bytes=0, seed=5,
                 n_sims=128, max_inflight=64):
     """Poisson stream of chemistry requests from many simulations (9 or 36
@@ -308,12 +323,17 @@ def serving_run(torch, chem, synth, device, n_requests, rate_frac=0.7, budget_by
         cands = [i for i in range(n_sims) if sims[i][0] == k and i not in busy]
         return cands[int(draw * len(cands)) % len(cands)] if cands else None
 
+    progress = [time.perf_counter()]
+
     def retire():
         for i, t in list(busy.items()):
             r = srv.poll(t)
             if r.state in (chem.REQ_DONE, chem.REQ_FAILED, chem.REQ_CANCELLED):
                 done.append((t, r, sims[i][1]))
                 del busy[i]
+                progress[0] = time.perf_counter()
+        if busy:
+            _stalled(progress[0])
 
     # capacity: a saturating burst
     done = []
@@ -398,7 +418,7 @@ def serving_background(torch, chem, synth, device, n_small=48, seed=7):
     torch.cuda.synchronize()
     srv = chem.Server()
     r, e = big[0].clone(), big[1].clone()
-    res = srv.wait(srv.submit(hs[36], r, e, 1e-6))
+    res = _wait_done(srv, srv.submit(hs[36], r, e, 1e-6))
     span_alone = (res.dev_last_ns - res.dev_first_ns) * 1e-9
     gaps = rng.exponential(0.8 * span_alone / n_small, n_small)
     r, e = big[0].clone(), big[1].clone()
@@ -409,10 +429,10 @@ def serving_background(torch, chem, synth, device, n_small=48, seed=7):
         while time.perf_counter() - t0 < at:
             time.sleep(0.0002)
         tickets.append(srv.submit(hs[k], rs, es, 1e-6))
-    rb = srv.wait(tb)
+    rb = _wait_done(srv, tb)
     lat, span, before = [], [], 0
     for t in tickets:
-        q = srv.wait(t)
+        q = _wait_done(srv, t)
         lat.append(q.t_done - q.t_submit)
         span.append((q.dev_last_ns - q.dev_first_ns) * 1e-9)
         before += q.dev_last_ns < rb.dev_last_ns

@@ -192,7 +192,7 @@ struct ServeQueue {
     const ServeDesc *desc;              // [cap], mapped host memory
     ServeDone *fin;                     // [cap], mapped host memory
     const unsigned long long *tail;     // mapped host: end of the last published chunk's real cells
-    unsigned long long *front;          // mapped host: a recent claim, for the host's window
+    unsigned long long *front;          // mapped host: the current chunk's first virtual cell, for the host's window
     const int *budget;                  // mapped host: this launch's blocks >= budget claim nothing
     ServeDesc *mdesc;                   // device [cap]: copies of the descriptors (seq -1: none)
     unsigned long long *dtail;          // device: the latest `tail` read

@@ -1121,7 +1121,11 @@ __device__ __forceinline__ long long ld_acquire_gpu(const long long *p) {
     return v;
 }
 // Refreshes the device copies of the host's `tail` and of this launch's
-// budget: at most one warp per launch every kServePollNs reads host memory.
+// budget, and tells the host where the hand-out of cells stands (`front`:
+// the first virtual cell of the current chunk; the cursor only grows, and
+// every claim attempt and every idle poll comes here, so the host sees the
+// claims catch up with what it published): at most one warp per launch
+// every kServePollNs.
 __device__ __forceinline__ void serve_refresh(const ServeQueue &q) {
     const unsigned long long now = globaltimer_ns();
     const unsigned long long last = ld_cg(q.dpoll);
@@ -1131,6 +1135,7 @@ __device__ __forceinline__ void serve_refresh(const ServeQueue &q) {
     __threadfence();   // what the host wrote before `tail`, before the copy of `tail`
     atomicMax(q.dtail, t);
     *reinterpret_cast<volatile int *>(q.dbudget) = bud;
+    *reinterpret_cast<volatile unsigned long long *>(q.front) = ld_cg(q.chunk) << kServeChunkLog;
 }
 // Copies the host descriptor of chunk c (ring entry ce) into the device ring;
 // called after a claim from the chunk succeeded, so the chunk is live and
@@ -1221,8 +1226,6 @@ __device__ __forceinline__ int serve_claim(const ServeQueue &q, int k, long long
                 const long long cnt = min((long long)k, nc - off);
                 v0 = (c << kServeChunkLog) + off;
                 e = ce;
-                if ((v0 >> 5) != ((v0 + cnt) >> 5))
-                    *reinterpret_cast<volatile unsigned long long *>(q.front) = (unsigned long long)(v0 + cnt);
                 return (int)cnt;
             }
         }

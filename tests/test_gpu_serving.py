@@ -25,6 +25,13 @@ def env():
     h36.close()
 
 
+def _wait(srv, t, timeout_s=60.0):
+    """A bounded wait: a request the server never finishes fails the test."""
+    res = srv.wait(t, timeout_us=int(timeout_s * 1e6))
+    assert res is not None, "request %d did not finish within %.0f s" % (t, timeout_s)
+    return res
+
+
 def _states(torch, mech, n, seed):
     f = synth.uniform_field(mech.ns, n, 900.0, 2800.0, seed=seed)
     rho, e = P.initial_state(mech, f)
@@ -53,7 +60,7 @@ def test_alone_equals_mixed(env):
     for ns, rho, e, dt in reqs:
         r, ev = rho.clone(), e.clone()
         t = srv.submit(mechs[ns][1], r, ev, dt)
-        res = srv.wait(t)
+        res = _wait(srv, t)
         assert res.state == chem.REQ_DONE
         alone.append((r, ev))
     # mixed: all submitted at once, overlapping on the device
@@ -65,7 +72,7 @@ def test_alone_equals_mixed(env):
         mixed.append((r, ev))
     spans = []
     for t in tickets:
-        res = srv.wait(t)
+        res = _wait(srv, t)
         assert res.state == chem.REQ_DONE
         assert 0 < res.dev_first_ns <= res.dev_last_ns
         spans.append((res.dev_first_ns, res.dev_last_ns))
@@ -111,12 +118,40 @@ def test_ring_laps_and_chunk_edges(env):
             tickets.append(srv.submit(h, r, e, dt))
             outs.append((n, r, e))
         for t in tickets:
-            assert srv.wait(t).state == chem.REQ_DONE
+            res = srv.wait(t, timeout_us=20_000_000)
+            assert res is not None and res.state == chem.REQ_DONE
         for n, r, e in outs:
             assert torch.equal(r, refs[n][0]) and torch.equal(e, refs[n][1]), (k, n)
     st = srv.stats()
     assert st["failed"] == 0 and st["completed"] == rounds * len(sizes)
     assert st["queue_errors"] == 0
+    srv.close()
+
+
+def test_many_one_cell_requests(env):
+    """A stream of requests of one cell each: every chunk holds a single
+    real cell, so the host's publication window has to follow the kernels'
+    hand-out of chunks, not of cells (a window that waited for claims to
+    cross cell boundaries stalled here).  Bounded waits: a stall fails the
+    test instead of hanging it."""
+    torch, chem, mechs = env
+    m, h = mechs[9]
+    rho0, e0 = _states(torch, m, 1, seed=78)
+    dt = 1e-7
+    r_ref, e_ref = rho0.clone(), e0.clone()
+    h.advance(r_ref, e_ref, dt)
+    torch.cuda.synchronize()
+    srv = chem.Server(max_inflight=64)
+    outs = []
+    for _ in range(300):
+        r, e = rho0.clone(), e0.clone()
+        outs.append((srv.submit(h, r, e, dt), r, e))
+    for t, r, e in outs:
+        res = srv.wait(t, timeout_us=20_000_000)
+        assert res is not None and res.state == chem.REQ_DONE
+        assert torch.equal(r, r_ref) and torch.equal(e, e_ref)
+    st = srv.stats()
+    assert st["failed"] == 0 and st["queue_errors"] == 0
     srv.close()
 
 
@@ -145,11 +180,11 @@ def test_small_requests_join_a_running_grid(env):
     assert srv.poll(tb).state == chem.REQ_RUNNING
     work = [(r.clone(), e.clone()) for r, e in smalls]
     ts = [srv.submit(h, r, e, 1e-6) for r, e in work]
-    res_b = srv.wait(tb)
+    res_b = _wait(srv, tb)
     assert res_b.state == chem.REQ_DONE
     inside = 0
     for t, (r, e), (rr, ee) in zip(ts, work, refs):
-        res = srv.wait(t)
+        res = _wait(srv, t)
         assert res.state == chem.REQ_DONE
         assert torch.equal(r, rr) and torch.equal(e, ee)
         assert res.dev_first_ns > res_b.dev_first_ns
@@ -183,9 +218,9 @@ def test_two_mechanisms_share_the_device(env):
     time.sleep(0.03)
     assert srv.poll(tb).state == chem.REQ_RUNNING
     ts = [srv.submit(h9, r, e, 1e-6) for r, e in smalls]
-    res_b = srv.wait(tb)
+    res_b = _wait(srv, tb)
     for t, (r, e), (rr, ee) in zip(ts, smalls, refs):
-        res = srv.wait(t)
+        res = _wait(srv, t)
         assert res.state == chem.REQ_DONE
         assert res.dev_last_ns < res_b.dev_last_ns
         assert torch.equal(r, rr) and torch.equal(e, ee)
@@ -199,10 +234,10 @@ def test_host_requests_match_device(env):
     rho, e = _states(torch, m, 5000, seed=7)
     srv = chem.Server()
     r_dev, e_dev = rho.clone(), e.clone()
-    srv.wait(srv.submit(h, r_dev, e_dev, 1e-6))
+    _wait(srv, srv.submit(h, r_dev, e_dev, 1e-6))
     r_h, e_h = rho.cpu().numpy().copy(), e.cpu().numpy().copy()
     status = np.full(5000, -1, np.int32)
-    res = srv.wait(srv.submit(h, r_h, e_h, 1e-6, host=True, status=status))
+    res = _wait(srv, srv.submit(h, r_h, e_h, 1e-6, host=True, status=status))
     assert res.state == chem.REQ_DONE
     assert np.array_equal(r_h, r_dev.cpu().numpy()) and np.array_equal(e_h, e_dev.cpu().numpy())
     assert (status == 0).all()
@@ -250,8 +285,8 @@ def test_cancel_wait_timeout_and_errors(env):
     assert srv.wait(t_q, timeout_us=1) is None                 # still queued behind t_long
     srv.cancel(t_c)
     assert srv.poll(t_c).state == chem.REQ_CANCELLED
-    assert srv.wait(t_q).state == chem.REQ_DONE
-    assert srv.wait(t_long).state == chem.REQ_DONE
+    assert _wait(srv, t_q).state == chem.REQ_DONE
+    assert _wait(srv, t_long).state == chem.REQ_DONE
     assert not torch.equal(q_r, q_r0)
     assert torch.equal(c_state[0], c0)                         # the cancelled state is untouched
     with pytest.raises(chem.ChemError) as ei:
