@@ -274,12 +274,16 @@ int chem_launch_count(chem_handle_t h, int64_t *count);
  * state); the scheduler admits the head of the FIFO queue when fewer than
  * max_inflight requests are admitted and unfinished and its bytes
  * (n_cells * (8 N_s + 20) + 1024) fit in the remaining budget, and publishes
- * its cells to its lane.  Slots of a running kernel that free up claim the
- * next published cell of whichever request comes next, so a request admitted
- * while others run is stepped inside the same grid, cells of several requests
- * in flight together on every SM (continuous batching on the device).  Lanes
- * of different mechanisms share the GPU: each lane with work gets an equal
- * share of its full grid.  Device-resident states (host = 0) are stepped in
+ * its cells to its lane in chunks of at most 1024, the request with the
+ * fewest cells left first (one waiting 50 ms without a chunk goes first),
+ * keeping about a quarter of the lane's slots worth of cells published ahead
+ * of the kernels.  The free slots of a warp of a running kernel claim
+ * consecutive published cells together, so a request admitted while others
+ * run is stepped inside the same grid, cells of several requests in flight
+ * together on every SM (continuous batching on the device).  Lanes of
+ * different mechanisms share the GPU: each lane with work gets an equal share
+ * of its full grid.  A server holds at most 16 lanes: a request that would
+ * need a 17th finishes FAILED with error CHEM_E_UNSUPPORTED.  Device-resident states (host = 0) are stepped in
  * place and count against the budget while in flight; host states (host = 1)
  * are copied through the pool and back.  A request is computed exactly as by
  * chem_advance_ex with the same handle, whatever else is in flight.
