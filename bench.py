@@ -36,12 +36,12 @@ WORKLOAD_DESC = ("synthetic 36 sp / 308 rxn mechanism (4 elements, 40 third-body
 # single-pass ncu capture of a full-size launch of the current kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum; part of the state written
 # back is still in L2 when the kernel ends).  Other workloads report null.
-MEASURED_TRAFFIC = {"mixed": 79.99e6 + 30.85e6, "fp64": 80.05e6 + 35.04e6}
+MEASURED_TRAFFIC = {"mixed": 80.06e6 + 29.98e6, "fp64": 80.23e6 + 34.77e6}
 # FP64-pipe utilisation of the step kernels from ncu
 # (sm__pipe_fp64_cycles_active, share of active cycles), captured on the
 # first 16,384 cells of the default workload (a full launch is too long for
 # a multi-pass capture).
-MEASURED_FP64_PIPE = {"mixed": 0.585, "fp64": 0.805}
+MEASURED_FP64_PIPE = {"mixed": 0.597, "fp64": 0.805}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk x 2 x max clock
 FP64_PEAK_PROBE_TFLOPS = 1.193                    # DFMA timing probe on this GPU model
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FFMA/clk x 2 x max clock

@@ -174,12 +174,13 @@ struct HostTables {
     std::vector<int2> j_meta;
     std::vector<int> j_nu, sp_nui, j_sk32, j_ptr32, j_d32;
     struct Layout {
-        std::vector<int2> j_meta, j_meta32, it_meta;
+        std::vector<int2> j_meta, it_meta;
+        std::vector<int4> j_meta32;
         std::vector<unsigned> j_w, sp_w;
         std::vector<int> j_d;
         std::vector<double> j_c;
     } lay[kLayouts];
-    int nD = 0, nD_F = 0, nD_B = 0, nD_FB = 0, nJ = 0, n_items = 0, ntb = 0;
+    int nD = 0, nD_F = 0, nD_B = 0, nD_FB = 0, nJ = 0, nJ_nz = 0, n_items = 0, ntb = 0;
 };
 
 // {1/F, ln F} at F = 1 + j/kLogTab, j = 0..kLogTab, rounded from extended
@@ -382,6 +383,7 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
         }
         t.j_ptr.push_back((int)t.j_d.size());
         t.j_ptr32.push_back((int)t.j_d32.size());
+        if (!lists[idx].empty()) t.nJ_nz++;   // (the empty lists come last)
     }
     // species lists (reactions with nu_rs != 0) in chunks of kChunk
     t.sp_item_ptr.assign(ns + 1, 0);
@@ -514,7 +516,19 @@ static void build_tables(const chem_mech_desc *d, HostTables &t) {
             L.j_d[pos[e]] = t.j_d[e];
             L.j_c[pos[e]] = t.j_c[e];
         }
-        const int nw32 = interleave(ns * ns, t.j_ptr32, G, L.j_meta32, pos, 16, &t.j_sk32, &t.j_d32);
+        std::vector<int2> meta32;
+        const int nw32 = interleave(ns * ns, t.j_ptr32, G, meta32, pos, 16, &t.j_sk32, &t.j_d32);
+        // the FP32 entries' metadata: first word, length, offset of (s, k)
+        // in the column-major matrix of columns of ldc rows, and the factor
+        // M_s / M_k rounded once to FP32
+        const int ldc = (ns + 3) & ~3;
+        for (const int2 &mt : meta32) {
+            const int s = (mt.y >> 8) & 0xff, k = mt.y & 0xff;
+            float f = (float)(d->molar_mass[s] / d->molar_mass[k]);
+            int fb;
+            std::memcpy(&fb, &f, sizeof fb);
+            L.j_meta32.push_back(make_int4(mt.x, mt.y >> 16, k * ldc + s, fb));
+        }
         L.j_w.assign(std::max(nw32, 1), 0u);
         for (size_t e = 0; e < pos.size(); ++e) L.j_w[pos[e]] = t.j_w[e];
         const int ni = interleave(t.n_items, t.it_ptr, G, L.it_meta, pos, 0, nullptr);
@@ -604,6 +618,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     m.nD_B = t.nD_B;
     m.nD_FB = t.nD_FB;
     m.nJ = t.nJ;
+    m.nJ_nz = t.nJ_nz;
     m.n_items = t.n_items;
     m.thermo = (const double *)at(i_th);
     m.tmid = (const double *)at(i_tm);
@@ -621,7 +636,7 @@ static int upload(const HostTables &t, int ns, int nr, Handle *h) {
     for (int li = 0; li < kLayouts; ++li) {
         GatherLayout &g = m.gl[li];
         g.j_meta = (const int2 *)at(i_lay[li][0]);
-        g.j_meta32 = (const int2 *)at(i_lay[li][7]);
+        g.j_meta32 = (const int4 *)at(i_lay[li][7]);
         g.j_w = (const unsigned *)at(i_lay[li][1]);
         g.j_d = (const int *)at(i_lay[li][2]);
         g.j_c = (const double *)at(i_lay[li][3]);

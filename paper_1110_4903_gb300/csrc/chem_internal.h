@@ -101,7 +101,7 @@ constexpr int kLogTab = 128;
 // one term per binary digit)
 struct GatherLayout {
     const int2 *j_meta;
-    const int2 *j_meta32;
+    const int4 *j_meta32;       // FP32 lists: {first word, length, matrix offset k ldc + s, (float)(M_s / M_k)}
     const unsigned *j_w;
     const int *j_d;
     const double *j_c;
@@ -118,6 +118,7 @@ struct DeviceMech {
     int ntb;                    // third-body reactions: the first ntb (internal order)
     int nD, nD_F, nD_B, nD_FB;  // group ends: [0,F) [F,B) [B,FB) [FB,nD)
     int nJ;                     // Jacobian entries gathered: ns*ns (species rows and columns)
+    int nJ_nz;                  //   of which the first nJ_nz have reaction terms (longest list first)
     int n_items;                // species-gather work items
     const double *thermo;       // [16][2][ns] (coefficient-major, above)
     const double *tmid;         // [ns] (positive: compared as integers)
@@ -250,7 +251,7 @@ constexpr int kBlockHeaderBytes = 0;
 //   JT        FP64 path: dTdr, w, u, rhs (ns each: the reduced system's
 //             temperature column factor, the T-derivative and third-body
 //             vectors, the right-hand side)
-//             FP32 path: w, u, es, rhs (ns each)
+//             FP32 path: w, u, rhs, es (ns each, padded to a multiple of 4)
 //   D region  first Q (nr doubles) and the species-gather partial sums (per
 //             item: sum nu Q in FP64, then sum nu dQ/dT and sum nu q_tb in JT),
 //             which are dead once the D entries (nD in JT) are written
@@ -281,8 +282,11 @@ __host__ __device__ inline long long slot_dbl_bytes(int ns, int jt) {
     const int n = ns + 1;
     return align16((2LL * n + (jt == 8 ? ns : 0)) * 8);
 }
+// the FP32 path's w, u, rhs and e_s arrays are padded to a multiple of four
+// entries, so that the Jacobian's dense part reads them as 16-byte vectors
+__host__ __device__ inline int small_stride(int ns, int jt) { return jt == 8 ? ns : (ns + 3) & ~3; }
 __host__ __device__ inline long long slot_small_bytes(int ns, int jt) {
-    return align16(4LL * ns * jt);
+    return align16(4LL * small_stride(ns, jt) * jt);
 }
 // species part of the union: c, em, emi (+ hRT) doubles, ek ints (+ cJ, hJ
 // floats), padded to 16 bytes so the per-reaction arrays that follow are

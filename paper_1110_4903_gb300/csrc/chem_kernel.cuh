@@ -25,8 +25,10 @@
 // energy, so the elimination runs on the ns species unknowns.  The mixed
 // path (JT = float) keeps the FP64 residual, rates, sources and
 // temperature, and moves everything that only feeds the Jacobian to FP32;
-// its LU is organised by columns.  It is bound by latency, so its slot
-// layout is cut to what it reads (20 warps per SM at 36 species).
+// it writes the Jacobian's rank-two part and the identity densely, four
+// rows per store, then adds the sparse reaction sums, and its LU is
+// organised by columns.  It is bound by latency, so its slot layout is cut
+// to what it reads (20 warps per SM at 36 species).
 //   Code size: with 20 warps at different phases, the instructions of one
 // Newton iteration have to stay in the SM's instruction caches.  The
 // compiler's unrolling of the many short runtime-count loops made the mixed
@@ -490,15 +492,16 @@ struct SlotMem {
         es = jt == 8 ? x0 + n : nullptr;
         char *q = base + slot_dbl_bytes(ns, jt);
         JT *t = reinterpret_cast<JT *>(q);
+        const int ss = small_stride(ns, jt);
         w = t;
-        u = w + ns;
-        rhs = u + ns;
+        u = w + ss;
+        rhs = u + ss;
         if (jt == 8) {
-            dTdr = rhs + ns;
+            dTdr = rhs + ss;
             esJ = reinterpret_cast<JT *>(es);
         } else {
             dTdr = nullptr;
-            esJ = rhs + ns;
+            esJ = rhs + ss;
         }
         q += slot_small_bytes(ns, jt);
         // D region: Q and the gather partials until the D entries replace them
@@ -850,45 +853,85 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
         for (int i = sl; i < N; i += G) sm.A[ix(i, N)] = fma(sm.w[i], cRE, sm.rhs[i]);
     }
 
-    // 6. the reduced system's -h J'_sk = -h (J_sk - w_s e_f,k dT/de)
-    //    (longest gather lists first, so the lanes of a pass run lists of
-    //    nearly equal length; four terms in flight per trip, two
-    //    accumulators)
+    // 6. the reduced system's -h J'_sk = -h (J_sk - w_s e_f,k dT/de), plus
+    //    the identity.  J_sk = w_s dT/drho_k + (u_s + M_s sum_r nu_rs D_rk) / M_k
+    //    (the D entries carry the factor M_k): a rank-two part, in which
+    //    the reduced system's column factor dT/drho_k - e_f,k dT/de stands
+    //    for dT/drho_k, plus the gathered sums (longest gather lists
+    //    first, so the lanes of a pass run lists of nearly equal length;
+    //    four terms in flight per trip, two accumulators)
     const JT *__restrict__ Dv = sm.D;
+    if constexpr (f32) {
+        // 6a. the rank-two part and the identity, dense: a lane writes
+        //     rows 4g..4g+3 of column k with one 16-byte store, from
+        //     16-byte reads of w and u (the padding rows of a column take
+        //     values that nothing reads).  Task t = k ldc/4 + g steps by G,
+        //     the carry taken without a division.
+        const int NG = ldc >> 2;
+        const unsigned rc = __ldg(m.div16 + NG);
+        int k = (int)(((unsigned)sl * rc) >> 16), g = sl - k * NG;
+        const int dk = (int)(((unsigned)G * rc) >> 16), dg = G - dk * NG;
+        const float cTe = -(mh * dTdef);
 #pragma unroll 1
-    for (int p = sl; p < m.nJ; p += G) {
-        const int2 meta = __ldg((f32 ? gl.j_meta32 : gl.j_meta) + p);
-        const int len = meta.y >> 16;
-        const int s = (meta.y >> 8) & 0xff, k = meta.y & 0xff;
-        const JT invMk = f32 ? (JT)__ldg(m.spf + k * kSpStride + 1) : (JT)__ldg(m.sp + k * kSpStride + 1);
-        // (the reduced system's column k: dT/drho_k - e_f,k dT/de)
-        const JT dTdrk = f32 ? -sm.esJ[k] * (JT)dTdef : sm.dTdr[k];
-        JT J = sm.w[s] * dTdrk;
-        JT a0 = 0, a1 = 0;
-        int e = meta.x, q = 0;
-        if (f32) {
-            // M_s sum nu_rs D_rk
-            // (the word's top nine bits are those of the float coefficient)
-            auto coef = [](unsigned wv) -> JT { return (JT)__int_as_float((int)(wv & 0xff800000u)); };
+        while (k < N) {
+            const float cT = cTe * sm.esJ[k], cU = mh * __ldg(m.spf + k * kSpStride + 1);
+            const float4 wv = *reinterpret_cast<const float4 *>(sm.w + 4 * g);
+            const float4 uv = *reinterpret_cast<const float4 *>(sm.u + 4 * g);
+            const int dd = k - 4 * g;   // the diagonal's row within the four
+            float4 a;
+            a.x = fmaf(wv.x, cT, uv.x * cU) + (dd == 0 ? 1.f : 0.f);
+            a.y = fmaf(wv.y, cT, uv.y * cU) + (dd == 1 ? 1.f : 0.f);
+            a.z = fmaf(wv.z, cT, uv.z * cU) + (dd == 2 ? 1.f : 0.f);
+            a.w = fmaf(wv.w, cT, uv.w * cU) + (dd == 3 ? 1.f : 0.f);
+            *reinterpret_cast<float4 *>(sm.A + k * ldc + 4 * g) = a;
+            k += dk;
+            g += dg;
+            if (g >= NG) {
+                g -= NG;
+                ++k;
+            }
+        }
+        __syncwarp();
+        // 6b. the gathered sums of the entries that have reaction terms,
+        //     added as -h (M_s / M_k) sum_r nu_rs D_rk
+        //     (the word's top nine bits are those of the float coefficient)
+        auto coef = [](unsigned wv) -> float { return __int_as_float((int)(wv & 0xff800000u)); };
+#pragma unroll 1
+        for (int p = sl; p < m.nJ_nz; p += G) {
+            const int4 meta = __ldg(gl.j_meta32 + p);
+            const int len = meta.y;
+            float a0 = 0.f, a1 = 0.f;
+            int e = meta.x, q = 0;
 #pragma unroll 1
             for (; q + 4 <= len; q += 4, e += 4 * G) {
                 const unsigned w0 = __ldg(gl.j_w + e), w1 = __ldg(gl.j_w + e + G), w2 = __ldg(gl.j_w + e + 2 * G),
                                w3 = __ldg(gl.j_w + e + 3 * G);
-                const JT v0 = Dv[w0 & 0x7fffffu], v1 = Dv[w1 & 0x7fffffu], v2 = Dv[w2 & 0x7fffffu],
-                         v3 = Dv[w3 & 0x7fffffu];
-                a0 = fma(coef(w0), v0, a0);
-                a1 = fma(coef(w1), v1, a1);
-                a0 = fma(coef(w2), v2, a0);
-                a1 = fma(coef(w3), v3, a1);
+                const float v0 = Dv[w0 & 0x7fffffu], v1 = Dv[w1 & 0x7fffffu], v2 = Dv[w2 & 0x7fffffu],
+                            v3 = Dv[w3 & 0x7fffffu];
+                a0 = fmaf(coef(w0), v0, a0);
+                a1 = fmaf(coef(w1), v1, a1);
+                a0 = fmaf(coef(w2), v2, a0);
+                a1 = fmaf(coef(w3), v3, a1);
             }
 #pragma unroll 1
             for (; q < len; ++q, e += G) {
                 const unsigned wv = __ldg(gl.j_w + e);
-                a0 = fma(coef(wv), Dv[wv & 0x7fffffu], a0);
+                a0 = fmaf(coef(wv), Dv[wv & 0x7fffffu], a0);
             }
-            // (D entries scaled by M_k: J_sk = w_s dT/drho_k + (u_s + M_s sum) / M_k)
-            J = fma(invMk, fma((JT)__ldg(m.spf + s * kSpStride), a0 + a1, sm.u[s]), J);
-        } else {
+            float *ap = reinterpret_cast<float *>(sm.A) + meta.z;
+            *ap = fmaf(mh * __int_as_float(meta.w), a0 + a1, *ap);
+        }
+        __syncwarp();
+    } else {
+#pragma unroll 1
+        for (int p = sl; p < m.nJ; p += G) {
+            const int2 meta = __ldg(gl.j_meta + p);
+            const int len = meta.y >> 16;
+            const int s = (meta.y >> 8) & 0xff, k = meta.y & 0xff;
+            const JT invMk = (JT)__ldg(m.sp + k * kSpStride + 1);
+            JT J = sm.w[s] * sm.dTdr[k];
+            JT a0 = 0, a1 = 0;
+            int e = meta.x, q = 0;
 #pragma unroll 1
             for (; q + 4 <= len; q += 4, e += 4 * G) {
                 const int d0 = __ldg(gl.j_d + e), d1 = __ldg(gl.j_d + e + G), d2 = __ldg(gl.j_d + e + 2 * G),
@@ -901,15 +944,15 @@ __device__ void newton_iteration(const DeviceMech &m, const double *tab, SlotMem
             }
 #pragma unroll 1
             for (; q < len; ++q, e += G) a0 = fma((JT)__ldg(gl.j_c + e), Dv[__ldg(gl.j_d + e)], a0);
-            // (D entries scaled by M_k: J_sk = w_s dT/drho_k + (u_s + sum) / M_k)
+            // (D entries scaled by M_k; the FP64 lists' coefficients are nu_rs M_s)
             J = fma(invMk, sm.u[s] + (a0 + a1), J);
+            sm.A[ix(s, k)] = mh * J;
         }
-        sm.A[ix(s, k)] = mh * J;
-    }
-    __syncwarp();
+        __syncwarp();
 #pragma unroll 1
-    for (int i = sl; i < N; i += G) sm.A[ix(i, i)] += (JT)1;
-    __syncwarp();
+        for (int i = sl; i < N; i += G) sm.A[ix(i, i)] += (JT)1;
+        __syncwarp();
+    }
 
     // 7. Gaussian elimination with row partial pivoting on [A | -F]
     //    (Sec. 3.2), ties to the lowest row; the pivot's reciprocal replaces

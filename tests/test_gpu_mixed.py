@@ -123,10 +123,15 @@ def test_mixed_full_size_sampled(torch, wl, sample, hot):
     ef = torch.tensor(P.oracle.OracleMech(m).ef(), device=dev)
     st, it, su, fa = (t.cpu().numpy() for t in outs)
     # conservation: BE conserves mass and U = e + sum e_f rho exactly at its
-    # root; the mixed path stops an accepted substep up to kappa x tolerance
-    # away from the root (contraction-rate stop), so each accepted substep may
-    # leave kappa (rtol + ns atol_rel) of relative mass or energy, carried on
-    bound = 1e-13 + torch.tensor(su, device=dev, dtype=torch.float64) * P.MIXED_OPTS["conv_kappa"] * (
+    # root; the mixed path stops an accepted substep when the contraction-rate
+    # estimate of its distance from the root, theta / (1 - theta) |delta|,
+    # is at most kappa x tolerance (Hairer & Wanner, Sec. IV.8), so each
+    # accepted substep may leave about kappa (rtol + ns atol_rel) of relative
+    # mass or energy, carried on.  The estimate takes the last contraction
+    # rate for the next one; with the FP32 Jacobian the rate varies between
+    # iterations, and the true distance can exceed the estimate: hence the
+    # factor 2 (the largest ratio measured over 2^18 cells is about 1.2)
+    bound = 1e-13 + 2 * torch.tensor(su, device=dev, dtype=torch.float64) * P.MIXED_OPTS["conv_kappa"] * (
         1e-10 + m.ns * 1e-12)
     assert (((rho.sum(0) - rho0.sum(0)).abs() / rho0.sum(0)) <= bound).all()
     U0, U1 = e0 + ef @ rho0, e + ef @ rho
